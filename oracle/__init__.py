@@ -1,0 +1,26 @@
+"""CPU oracle for inexact IETI-DP (Hofer, Langer, Takacs: "Inexact Dual-Primal
+Isogeometric Tearing and Interconnecting Methods").
+
+TEST INFRASTRUCTURE ONLY.  Only the test suite, ``__graft_entry__.smoke()``
+and the CPU-baseline leg of ``bench.py`` may import this package.  The product
+path (the CUDA library and its Python binding) never imports, links or runs it,
+and this package never imports the product path.  The one module both sides
+read is ``paper_1705_04531_gb300.workloads``, which only describes inputs.
+
+Everything here is plain, slow FP64 numpy/scipy written from the paper:
+
+* ``splines``   Cox-de Boor B-splines, tensor products, knot insertion (Sec. 2).
+* ``geometry``  patch maps (identity grid, exact NURBS quarter annulus) and the
+                model problem's right-hand sides (Eq. 1).
+* ``assembly``  Galerkin stiffness / load / parameter mass per patch (Eq. 1,
+                Sec. 3.2 for the parameter-domain mass).
+* ``domain``    multipatch numbering, the conforming global system and its
+                direct solve: the *definition* of the method's result.
+* ``multigrid`` geometric h-multigrid with Gauss-Seidel smoothing (Sec. 4).
+* ``ietidp``    tearing, jump operator, primal constraints, energy-minimizing
+                primal basis (Eq. 6), local Neumann solves (Eq. 7), scaled
+                Dirichlet preconditioner and the dual PCG for Eq. 4, in the
+                D-D (direct) and MG-MG (multigrid) variants of Sec. 3.3.
+
+Parity status of each function is stated in its module header.
+"""

@@ -1,0 +1,481 @@
+"""IETI-DP with energy-minimizing primal subspace, D-D and MG-MG variants
+(Sec. 2-4 of the paper).
+
+ORACLE (test infrastructure only).  Plain FP64 numpy/scipy, one patch at a
+time, in the order the paper states the algorithm.
+
+Notation follows the paper.  Per patch k: stiffness K (Dirichlet dofs of the
+global boundary removed), load f, constraint matrix C (n_Pi^(k) rows: vertex
+values, edge / face averages), primal selection A (global primal index of
+each row), local part of the jump operator B.
+
+* Tearing / jump operator (Sec. 2): one multiplier per pair of patches that
+  share an interface dof which is not a primal vertex (fully redundant), sign
+  +1 on the lower patch index; B_D scales each entry by 1/(number of patches
+  sharing the dof) (multiplicity scaling; the paper leaves the scaling open).
+* Energy-minimizing primal basis (Eq. 6): [K C^T; C 0][phi; mu] = [0; e_j].
+  D-D: sparse LU of the saddle matrix.  MG-MG: null-space method, phi_j =
+  psi_j + v_j with C psi_j = e_j and v_j in ker C solving
+  P_E K P_E v = -P_E K psi_j by CG preconditioned with P_E V P_E, where P_E
+  is the Euclidean projector on ker C (rows of C have disjoint supports) and
+  V a V-cycle on K (or K + 1e-2 M^ for patches that do not touch the
+  Dirichlet boundary, Sec. 3.2).  The paper uses Schoeberl-Zulehner CG here;
+  both give the solution of Eq. 6.
+* S_PiPi = sum_k A^T phi^T K phi A, dense Cholesky (Sec. 3.3: direct coarse
+  solve).
+* K~^{-1} g (block structure of Sec. 2): primal part
+  phi A S_PiPi^{-1} sum A^T phi^T g; Delta part per patch = minimizer of
+  1/2 w'Kw - w'g on ker C (Eq. 7).  D-D: the saddle LU.  MG-MG: CG on K with
+  right-hand side P^T g, P = I - phi C, V-cycle preconditioner, stopped at
+  relative residual tol_inner; then w = P z (Sec. 3.2: unconstrained solve
+  followed by the energy-minimizing projection).
+* F = B K~^{-1} B^T, d = B K~^{-1} f (Eq. 4); scaled Dirichlet preconditioner
+  M_sD^{-1} = B_D S B_D^T with S = K_BB - K_BI K_II^{-1} K_IB; K_II^{-1} exact
+  (D-D) or two V-cycles (MG-MG, Sec. 4).
+* Outer CG on F lambda = d, lambda_0 = 0, stop at ||r|| <= tol ||d||
+  (Sec. 4), then u = K~^{-1}(f - B^T lambda).  The condition number is
+  estimated from the CG coefficients (Lanczos tridiagonal).
+
+Pins (tests/test_oracle_ietidp.py): u equals the conforming global direct
+solve (domain.Multipatch.solve_global); B u = 0; C phi = I and phi^T K v = 0
+for v in ker C; MG-MG equals D-D; kappa grows like (1 + log(H/h))^2; a 1x1
+grid reduces to a single Dirichlet solve.  Iteration counts against the
+paper's tables: parity unpinned (the paper's geometries are not specified).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from . import multigrid, splines
+from .domain import Multipatch
+
+
+@dataclass
+class Options:
+    mode: str = "direct"          # "direct" (D-D) or "mg" (MG-MG)
+    tol_outer: float = 1e-10
+    tol_inner: float = 1e-12      # Neumann solves in F, d and the recovery
+    tol_basis: float = 1e-12      # primal basis
+    maxit_outer: int = 500
+    maxit_inner: int = 500
+    alpha: float = 1e-2           # K_M = K + alpha M^ for floating patches
+    dirichlet_vcycles: int = 2
+    nu1: int = 2
+    nu2: int = 2
+    cmin: int = 4
+
+
+@dataclass
+class Stats:
+    outer_it: int = 0
+    converged: bool = False
+    kappa: float = float("nan")
+    rel_res: float = float("nan")
+    neumann_its: list = field(default_factory=list)    # per patch per solve
+    basis_its: list = field(default_factory=list)
+    alphas: list = field(default_factory=list)
+    betas: list = field(default_factory=list)
+    d_norm: float = float("nan")
+    d_scale: float = float("nan")
+
+
+class IETIDP:
+    def __init__(self, dom, opts: Options | None = None):
+        self.dom = dom
+        self.o = opts or Options()
+        self.mp = Multipatch(dom)
+        self.stats = Stats()
+        Kfull, ffull, Mfull = self.mp.assemble()
+        self.Kfull = Kfull
+        d = dom.dim
+        N = dom.npatch
+        self.N = N
+        mp = self.mp
+        # --- per-patch free dofs (global Dirichlet boundary removed) -------
+        self.m = []
+        self.dmask = []
+        self.free = []
+        self.inv = []
+        self.K = []
+        self.f = []
+        for k in range(N):
+            c = dom.patch_coords(k)
+            m = tuple(dom.patch_nelem(k)[r] + dom.patch_degree(k)[r] for r in range(d))
+            mask = 0
+            for r in range(d):
+                if c[r] == 0:
+                    mask |= 1 << (2 * r)
+                if c[r] == dom.grid[r] - 1:
+                    mask |= 1 << (2 * r + 1)
+            fr = np.nonzero(multigrid.free_mask(m, mask))[0]
+            inv = -np.ones(int(np.prod(m)), dtype=np.int64)
+            inv[fr] = np.arange(len(fr))
+            self.m.append(m)
+            self.dmask.append(mask)
+            self.free.append(fr)
+            self.inv.append(inv)
+            self.K.append(sp.csr_matrix(Kfull[k][fr][:, fr]))
+            self.f.append(ffull[k][fr])
+        self.floating = [mk == 0 for mk in self.dmask]
+        self._build_interfaces()
+        self._build_primal()
+        self._build_jump()
+        if self.o.mode == "direct":
+            self._setup_direct()
+        else:
+            self._setup_mg()
+        self._setup_coarse()
+
+    # ------------------------------------------------------------------
+    def _build_interfaces(self):
+        """Global interface dofs grouped into vertices / edges / faces."""
+        mp, d = self.mp, self.dom.dim
+        ntype, onbp = mp.interface_type()
+        gi = mp.global_index_grid()
+        self.objects = {}                  # key -> list of global dofs
+        cand = np.nonzero((ntype > 0) & ~mp.dirichlet)[0]
+        for g in cand:
+            key = []
+            for r in range(d):
+                if onbp[r, g]:
+                    key.append(("bp", int(gi[r][g])))
+                else:
+                    key.append(("cell", mp.cell_of(r, int(gi[r][g]))))
+            self.objects.setdefault((int(ntype[g]), tuple(key)), []).append(int(g))
+        self.iface_global = cand
+        # interface (B-side) free-local dofs per patch
+        self.iface = []
+        isif = np.zeros(mp.nglob, dtype=bool)
+        isif[cand] = True
+        for k in range(self.N):
+            loc = self.free[k]
+            gl = mp.l2g[k][loc]
+            self.iface.append(np.nonzero(isif[gl])[0])
+
+    def _object_kind(self, ntype):
+        d = self.dom.dim
+        if ntype == d:
+            return "vertex"
+        if d == 2:
+            return "edge"
+        return "edge" if ntype == 2 else "face"
+
+    def _build_primal(self):
+        d = self.dom.dim
+        sel = set(self.dom.primal)
+        self.primal_objects = []
+        for key in sorted(self.objects.keys()):
+            kind = self._object_kind(key[0])
+            if kind in sel:
+                self.primal_objects.append((kind, key, self.objects[key]))
+        self.nPi = len(self.primal_objects)
+        self.vertex_dofs = set()
+        for kind, key, dofs in self.primal_objects:
+            if kind == "vertex":
+                self.vertex_dofs.update(dofs)
+        # per-patch C (rows over free-local dofs) and A (global primal index)
+        rows = [[] for _ in range(self.N)]
+        Aidx = [[] for _ in range(self.N)]
+        for j, (kind, key, dofs) in enumerate(self.primal_objects):
+            per_patch = {}
+            for g in dofs:
+                for (k, loc) in self.mp.copies(g):
+                    per_patch.setdefault(k, []).append(loc)
+            for k, locs in per_patch.items():
+                locs = np.array(locs)
+                row = np.zeros(len(self.free[k]))
+                if kind == "vertex":
+                    row[self.inv[k][locs]] = 1.0
+                else:
+                    tang = [r for r in range(d) if key[1][r][0] == "cell"]
+                    ti = multigrid.tensor_index(self.m[k], locs)
+                    w = np.ones(len(locs))
+                    deg = self.dom.patch_degree(k)
+                    nel = self.dom.patch_nelem(k)
+                    for r in tang:
+                        ints = splines.basis_integrals(nel[r], deg[r])
+                        w *= ints[ti[r]]
+                    row[self.inv[k][locs]] = w / w.sum()
+                rows[k].append(row)
+                Aidx[k].append(j)
+        self.C = []
+        self.A = []
+        for k in range(self.N):
+            n = len(self.free[k])
+            if rows[k]:
+                self.C.append(sp.csr_matrix(np.array(rows[k])))
+            else:
+                self.C.append(sp.csr_matrix((0, n)))
+            self.A.append(np.array(Aidx[k], dtype=np.int64))
+            if self.floating[k] and self.C[k].shape[0] == 0:
+                raise ValueError(f"floating patch {k} has no primal constraint")
+
+    def _build_jump(self):
+        """Multipliers: (patch_a, freeloc_a, patch_b, freeloc_b), +1 on a."""
+        lam = []
+        mult = [np.ones(len(self.free[k])) for k in range(self.N)]
+        for g in self.iface_global:
+            cps = self.mp.copies(int(g))
+            for (k, loc) in cps:
+                mult[k][self.inv[k][loc]] = len(cps)
+            if int(g) in self.vertex_dofs:
+                continue
+            for a in range(len(cps)):
+                for b in range(a + 1, len(cps)):
+                    ka, la = cps[a]
+                    kb, lb = cps[b]
+                    lam.append((ka, int(self.inv[ka][la]), kb, int(self.inv[kb][lb])))
+        self.lam = lam
+        self.nlam = len(lam)
+        self.mult = mult
+
+    def BT(self, lam_vec, scaled=False):
+        out = [np.zeros(len(self.free[k])) for k in range(self.N)]
+        for i, (ka, la, kb, lb) in enumerate(self.lam):
+            sa = 1.0 / self.mult[ka][la] if scaled else 1.0
+            sb = 1.0 / self.mult[kb][lb] if scaled else 1.0
+            out[ka][la] += sa * lam_vec[i]
+            out[kb][lb] -= sb * lam_vec[i]
+        return out
+
+    def Bop(self, u, scaled=False):
+        q = np.zeros(self.nlam)
+        for i, (ka, la, kb, lb) in enumerate(self.lam):
+            sa = 1.0 / self.mult[ka][la] if scaled else 1.0
+            sb = 1.0 / self.mult[kb][lb] if scaled else 1.0
+            q[i] = sa * u[ka][la] - sb * u[kb][lb]
+        return q
+
+    # ------------------------------------------------------------------
+    def _setup_direct(self):
+        self.kkt = []
+        self.phi = []
+        self.KII = []
+        for k in range(self.N):
+            K, C = self.K[k], self.C[k]
+            npi = C.shape[0]
+            M = sp.bmat([[K, C.T], [C, None]], format="csc") if npi else sp.csc_matrix(K)
+            lu = spla.splu(M)
+            self.kkt.append(lu)
+            n = K.shape[0]
+            rhs = np.zeros((n + npi, npi))
+            rhs[n:, :] = np.eye(npi)
+            self.phi.append(lu.solve(rhs)[:n, :] if npi else np.zeros((n, 0)))
+            I = self._interior(k)
+            self.KII.append(spla.splu(sp.csc_matrix(self.K[k][I][:, I])) if len(I) else None)
+
+    def _interior(self, k):
+        isB = np.zeros(len(self.free[k]), dtype=bool)
+        isB[self.iface[k]] = True
+        return np.nonzero(~isB)[0]
+
+    def _setup_mg(self):
+        o = self.o
+        self.hier, self.mgN, self.mgD, self.phi = [], [], [], []
+        d = self.dom.dim
+        allsides = (1 << (2 * d)) - 1
+        for k in range(self.N):
+            h = multigrid.Hierarchy(self.Kfull[k], self.dom.patch_nelem(k),
+                                    self.dom.patch_degree(k), o.cmin)
+            self.hier.append(h)
+            alpha = o.alpha if self.floating[k] else 0.0
+            self.mgN.append(multigrid.MGOperator(h, self.dmask[k], alpha, o.nu1, o.nu2))
+            self.mgD.append(multigrid.MGOperator(h, allsides, 0.0, o.nu1, o.nu2))
+            self.phi.append(self._basis_mg(k))
+
+    def _projector(self, k):
+        C = self.C[k]
+        Cd = C.toarray()
+        nrm = np.einsum("ij,ij->i", Cd, Cd)
+
+        def proj(x):
+            if C.shape[0] == 0:
+                return x
+            return x - C.T @ ((C @ x) / nrm)
+        return proj
+
+    def _basis_mg(self, k):
+        C, K = self.C[k], self.K[k]
+        npi = C.shape[0]
+        n = K.shape[0]
+        phi = np.zeros((n, npi))
+        PE = self._projector(k)
+        V = self.mgN[k].vcycle
+        for j in range(npi):
+            psi = (C[j].toarray().ravel() != 0).astype(np.float64)
+            b = -PE(K @ psi)
+            v, it, ok = multigrid.pcg(lambda x: PE(K @ x), b, lambda r: V(r),
+                                      self.o.tol_basis, self.o.maxit_inner, project=PE)
+            self.stats.basis_its.append(it)
+            phi[:, j] = psi + v
+        return phi
+
+    def _setup_coarse(self):
+        S = np.zeros((self.nPi, self.nPi))
+        for k in range(self.N):
+            if self.C[k].shape[0] == 0:
+                continue
+            Sl = self.phi[k].T @ (self.K[k] @ self.phi[k])
+            A = self.A[k]
+            S[np.ix_(A, A)] += Sl
+        self.SPiPi = S
+        self.cholS = sla.cho_factor(S) if self.nPi else None
+
+    # ------------------------------------------------------------------
+    def delta_solve(self, k, g):
+        """Minimizer of 1/2 w'Kw - w'g over ker C (Eq. 7)."""
+        C, phi = self.C[k], self.phi[k]
+        npi = C.shape[0]
+        if self.o.mode == "direct":
+            if npi == 0:
+                return self.kkt[k].solve(g)
+            rhs = np.concatenate([g, np.zeros(npi)])
+            return self.kkt[k].solve(rhs)[: len(g)]
+        b = g - C.T @ (phi.T @ g) if npi else g.copy()
+        z, it, ok = multigrid.pcg(lambda x: self.K[k] @ x, b, self.mgN[k].vcycle,
+                                  self.o.tol_inner, self.o.maxit_inner)
+        self.stats.neumann_its.append(it)
+        return z - phi @ (C @ z) if npi else z
+
+    def Ktilde_inv(self, g):
+        rPi = np.zeros(self.nPi)
+        for k in range(self.N):
+            if len(self.A[k]):
+                np.add.at(rPi, self.A[k], self.phi[k].T @ g[k])
+        uPi = sla.cho_solve(self.cholS, rPi) if self.nPi else rPi
+        out = []
+        for k in range(self.N):
+            u = self.delta_solve(k, g[k])
+            if len(self.A[k]):
+                u = u + self.phi[k] @ uPi[self.A[k]]
+            out.append(u)
+        return out
+
+    def F(self, lam):
+        return self.Bop(self.Ktilde_inv(self.BT(lam)))
+
+    def schur_apply(self, k, v):
+        """(S v) on the interface dofs of patch k, v given on all free dofs
+        (zero off the interface)."""
+        I = self._interior(k)
+        K = self.K[k]
+        t = -(K[I] @ v)
+        if self.o.mode == "direct":
+            xI = self.KII[k].solve(t) if len(I) else t
+        else:
+            V = self.mgD[k]
+            KII = K[I][:, I]
+            xI = V.vcycle(t)
+            for _ in range(self.o.dirichlet_vcycles - 1):
+                xI = xI + V.vcycle(t - KII @ xI)
+        full = v.copy()
+        full[I] += xI
+        out = np.zeros_like(v)
+        B = self.iface[k]
+        out[B] = K[B] @ full
+        return out
+
+    def precond(self, r):
+        v = self.BT(r, scaled=True)
+        w = [self.schur_apply(k, v[k]) for k in range(self.N)]
+        return self.Bop(w, scaled=True)
+
+    def solve(self):
+        st = self.stats
+        fr = self.f
+        if self.nlam == 0:
+            u = self.Ktilde_inv(fr)
+            st.converged = True
+            return self._expand(u)
+        u0 = self.Ktilde_inv(fr)
+        d = self.Bop(u0)
+        lam = np.zeros(self.nlam)
+        r = d.copy()
+        nd = np.linalg.norm(d)
+        # jump scale of the torn solution u0 = K~^{-1} f: d = B u0 vanishes
+        # identically for mirror-symmetric problems, where only rounding
+        # noise is left; the torn solution is then accepted (lambda = 0).
+        scale = jump_scale(self.lam, u0)
+        st.d_norm, st.d_scale = nd, scale
+        if nd <= self.o.tol_outer * scale:
+            st.converged = True
+        else:
+            z = self.precond(r)
+            p = z.copy()
+            rz = r @ z
+            for it in range(1, self.o.maxit_outer + 1):
+                q = self.F(p)
+                alpha = rz / (p @ q)
+                lam += alpha * p
+                r -= alpha * q
+                st.alphas.append(alpha)
+                st.outer_it = it
+                st.rel_res = np.linalg.norm(r) / nd
+                if st.rel_res <= self.o.tol_outer:
+                    st.converged = True
+                    break
+                z = self.precond(r)
+                rz_new = r @ z
+                beta = rz_new / rz
+                st.betas.append(beta)
+                rz = rz_new
+                p = z + beta * p
+        st.kappa = lanczos_kappa(st.alphas, st.betas)
+        bt = self.BT(lam)
+        u = self.Ktilde_inv([fr[k] - bt[k] for k in range(self.N)])
+        self.lam_sol = lam
+        return self._expand(u)
+
+    def _expand(self, u):
+        """Free-local patch vectors -> full local tensor grids."""
+        out = []
+        for k in range(self.N):
+            full = np.zeros(int(np.prod(self.m[k])))
+            full[self.free[k]] = u[k]
+            out.append(full)
+        return out
+
+    def jump(self, u_full):
+        u = [u_full[k][self.free[k]] for k in range(self.N)]
+        return self.Bop(u)
+
+
+def jump_scale(lam, u):
+    """sqrt(sum over multipliers of u_a^2 + u_b^2): the size of the values
+    whose differences the jump operator takes."""
+    s = 0.0
+    for (ka, la, kb, lb) in lam:
+        s += u[ka][la] ** 2 + u[kb][lb] ** 2
+    return float(np.sqrt(s))
+
+
+def lanczos_kappa(alphas, betas):
+    """Condition estimate from CG coefficients: T_kk = 1/a_k + b_{k-1}/a_{k-1},
+    T_k,k+1 = sqrt(b_k)/a_k; kappa = lambda_max(T)/lambda_min(T)."""
+    n = len(alphas)
+    if n == 0:
+        return 1.0
+    T = np.zeros((n, n))
+    for k in range(n):
+        T[k, k] = 1.0 / alphas[k]
+        if k > 0:
+            T[k, k] += betas[k - 1] / alphas[k - 1]
+        if k < n - 1 and k < len(betas):
+            T[k, k + 1] = T[k + 1, k] = np.sqrt(betas[k]) / alphas[k]
+    ev = np.linalg.eigvalsh(T)
+    return float(ev[-1] / ev[0])
+
+
+def global_from_patches(mp: Multipatch, u_patches):
+    """Average torn copies into the global coefficient vector."""
+    acc = np.zeros(mp.nglob)
+    cnt = np.zeros(mp.nglob)
+    for k, u in enumerate(u_patches):
+        np.add.at(acc, mp.l2g[k], u)
+        np.add.at(cnt, mp.l2g[k], 1.0)
+    return acc / np.maximum(cnt, 1)
