@@ -1,0 +1,229 @@
+/*
+ * ietidp.h -- C ABI of the GB300 inexact IETI-DP library.
+ *
+ * The library solves the model problem of Eq. 1 (-Laplace u = f in Omega,
+ * u = 0 on the boundary, a(u,v) = <F,v>) discretized with B-splines on a
+ * multipatch domain (Sec. 2) by the dual-primal tearing and interconnecting
+ * method with an energy-minimizing primal space, in the MG-MG variant of
+ * Sec. 3.3: every local problem (the S-orthogonal primal basis of Eq. 6, the
+ * local Neumann problems of Eq. 7 inside F = B K~^{-1} B^T, and the local
+ * Dirichlet problems of the scaled Dirichlet preconditioner of Sec. 2/3.1)
+ * is solved by geometric multigrid on the GPU.
+ *
+ * Conventions shared by every entry point:
+ *  - return value: 0 on success, a negative IETIDP_E_* code on failure;
+ *    ietidp_last_error() gives a message (library-owned, valid until the
+ *    next call on the same thread);
+ *  - the caller owns every array it passes; the library copies what it keeps;
+ *  - the library owns the handles it returns and all device memory behind
+ *    them; *_destroy / *_free release them;
+ *  - "device" pointers are CUDA global-memory pointers on the current
+ *    device, "host" pointers ordinary memory; sizes are element counts;
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream); all device
+ *    work of a handle is ordered on the stream given when it was created;
+ *  - invalid descriptors are rejected before any device work; no entry point
+ *    traps the device; iterative solvers that hit their iteration limit
+ *    return IETIDP_E_NOT_CONVERGED with the statistics filled in.
+ *
+ * Torn vector layout ("patch layout"): patch after patch, each patch's
+ * coefficients on its full tensor grid of (n_r + p_r) functions per
+ * direction, first direction fastest, including the coefficients of the
+ * Dirichlet boundary (which are always 0 in a solution).  ietidp_info
+ * returns the per-patch offsets.
+ */
+#ifndef IETIDP_H
+#define IETIDP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------ */
+#define IETIDP_OK               0
+#define IETIDP_E_INVALID_ARG   -1
+#define IETIDP_E_OOM           -2   /* device allocation failed            */
+#define IETIDP_E_BUDGET        -3   /* request does not fit a memory budget */
+#define IETIDP_E_CUDA          -4   /* a CUDA runtime call failed           */
+#define IETIDP_E_NOT_CONVERGED -5   /* an iteration limit was reached       */
+#define IETIDP_E_TIMEOUT       -6   /* a bounded device wait expired        */
+#define IETIDP_E_NONFINITE     -7   /* NaN/Inf in input or iteration        */
+#define IETIDP_E_BREAKDOWN     -8   /* CG breakdown / coarse matrix not SPD */
+
+/* ---- geometry kinds (Sec. 2: each patch is the image of (0,1)^d) ------- */
+#define IGA_GEO_BOX      0   /* affine: x_r = lo_r + (hi_r - lo_r) xi_r        */
+#define IGA_GEO_ANNULUS  1   /* quarter annulus: (s1,s2) = lo + (hi-lo) xi is a
+                                sub-box of the parameter square of the exact map
+                                G(s1,s2) = (1 + s2) C(s1), C the rational
+                                quadratic quarter circle from (1,0) to (0,1)
+                                with weights (1, 1/sqrt 2, 1)               */
+
+/* ---- right-hand sides of Eq. 1 ---------------------------------------- */
+#define IGA_RHS_NONE     0   /* zero load (solve takes a load vector)          */
+#define IGA_RHS_SIN2D    1   /* 2 pi^2 sin(pi x) sin(pi y)                     */
+#define IGA_RHS_SIN3D    2   /* 3 pi^2 sin(pi x) sin(pi y) sin(pi z)           */
+#define IGA_RHS_ANNULUS  3   /* -Laplace of sin(pi x) sin(pi y) (r-1)(2-r)     */
+#define IGA_RHS_MODES    4   /* sum_j a_j sin(k_j pi x) sin(l_j pi y)          */
+#define IGA_RHS_QUAD     5   /* f given at every Gauss point (see below)       */
+
+/* ---- primal constraint set (Sec. 4: vertex values, edge/face averages) - */
+#define IETIDP_PRIMAL_VERTEX 1u
+#define IETIDP_PRIMAL_EDGE   2u
+#define IETIDP_PRIMAL_FACE   4u
+
+/* ---- precision of the multigrid V-cycles -------------------------------- */
+#define IETIDP_PREC_FP64   0  /* everything FP64                             */
+#define IETIDP_PREC_MIXED  1  /* V-cycles (smoother, SpMV, transfers) FP32;
+                                 inner/outer CG, residuals, dots, primal
+                                 coarse Cholesky FP64                        */
+
+typedef struct {
+    int    degree[3];   /* spline degree p_r >= 1 per direction (d entries)   */
+    int    nelem[3];    /* uniform elements n_r >= 1 per direction            */
+    int    geo_kind;    /* IGA_GEO_*                                          */
+    double lo[3];       /* box corner (physical for BOX, parameter for ANNULUS)*/
+    double hi[3];
+} iga_patch_desc;
+
+/* Side numbering: side 2r is xi_r = 0, side 2r+1 is xi_r = 1.  The tangential
+ * directions of a side are the remaining directions in increasing order.
+ * Interfaces are conforming (Sec. 2): both sides carry the same tangential
+ * spline space.  `swap` (3D only) exchanges the two tangential directions of
+ * side_b, and flip[t] reverses tangential direction t of side_b (after the
+ * swap), relative to side_a. */
+typedef struct {
+    int patch_a, side_a, patch_b, side_b;
+    int flip[2];
+    int swap;
+} iga_interface_desc;
+
+typedef struct {
+    int dim;                                 /* 2 or 3                          */
+    int npatch;
+    const iga_patch_desc*     patches;       /* host, npatch entries            */
+    int ninterface;
+    const iga_interface_desc* interfaces;    /* host, ninterface entries        */
+    /* Every patch side that is not part of an interface lies on the boundary
+     * of Omega and carries the homogeneous Dirichlet condition of Eq. 1. */
+    int rhs_kind;                            /* IGA_RHS_*                       */
+    int nmodes;                              /* IGA_RHS_MODES                   */
+    const double* mode_a;                    /* host, nmodes                    */
+    const int*    mode_k;
+    const int*    mode_l;
+    /* IGA_RHS_QUAD: f at the tensor grid of Gauss points of every patch
+     * (n_r (p_r + 1) points per direction, p_r + 1 Gauss-Legendre points per
+     * element, first direction fastest), patch after patch.  Device. */
+    const double* quad_values;
+} iga_domain_desc;
+
+typedef struct iga_problem   iga_problem;
+typedef struct ietidp_handle ietidp_handle;
+
+typedef struct {
+    unsigned primal;          /* IETIDP_PRIMAL_* bitmask                       */
+    int    precision;         /* IETIDP_PREC_*                                 */
+    double tol_outer;         /* dual PCG: ||d - F lambda|| <= tol ||d||  (1e-10) */
+    double tol_inner;         /* local Neumann solves, relative residual (1e-12) */
+    double tol_basis;         /* primal basis solves, relative residual  (1e-12) */
+    int    maxit_outer;       /* (500)                                         */
+    int    maxit_inner;       /* (500)                                         */
+    int    nu_pre, nu_post;   /* smoothing steps (2, 2)                        */
+    int    coarse_elems;      /* coarsen while a direction has more elements (4) */
+    int    dirichlet_vcycles; /* V-cycles for K_II^{-1} in the preconditioner (2) */
+    double alpha_reg;         /* K_M = K + alpha M^ on floating patches (1e-2)  */
+    int    cluster;           /* CTAs per local problem (0 = autotune)         */
+} ietidp_options;
+
+typedef struct {
+    int    outer_it;          /* dual PCG iterations                           */
+    int    converged;
+    double rel_res;           /* final ||r|| / ||d||                           */
+    double kappa;             /* Lanczos estimate from the CG coefficients     */
+    double d_norm, d_scale;   /* ||d|| and the jump scale of K~^{-1} f         */
+    double inner_it_avg;      /* Neumann solves: mean CG iterations per patch   */
+    int    inner_it_max;
+    double basis_it_avg;      /* primal basis: mean CG iterations per function */
+    int    basis_it_max;
+    long long vcycles;        /* V-cycles executed (all patches)               */
+    long long vcycle_dofs;    /* sum over V-cycles of fine-level dofs          */
+    double t_setup_ms, t_solve_ms;
+} ietidp_stats;
+
+typedef struct {
+    int    dim, npatch;
+    long long n_torn;         /* length of a torn vector (patch layout)         */
+    int    n_lambda;          /* Lagrange multipliers                          */
+    int    n_primal;          /* primal dofs (size of S_PiPi)                   */
+    int    n_floating;        /* patches without a Dirichlet side               */
+    int    max_levels;
+    long long device_bytes;   /* device memory held by the handle              */
+} ietidp_info;
+
+/* Fill `opt` with the defaults quoted above. */
+void ietidp_default_options(ietidp_options* opt);
+
+/* Assemble the per-patch Galerkin stiffness K^(k) and load f^(k) of Eq. 1
+ * with the pulled-back B-spline basis (Sec. 2), Gauss quadrature with p_r+1
+ * points per element and direction, on the GPU.  Builds the patch topology
+ * (interfaces, Dirichlet sides, conforming dof identification) on the host.
+ * `out` receives a new problem; free it with iga_problem_free. */
+int iga_assemble_patches(const iga_domain_desc* dom, void* stream, iga_problem** out);
+
+/* The assembled load vector f~ in patch layout (device, n_torn doubles). */
+int iga_problem_load(const iga_problem* prob, double* f_out);
+int iga_problem_free(iga_problem* prob);
+
+/* IETI-DP setup (Sec. 2, 3.2, 4): jump operator B and scaled B_D, primal
+ * constraints C^(k), multigrid hierarchies (Galerkin coarse operators,
+ * regularized K + alpha M^ on floating patches, coarsest-level factors),
+ * the energy-minimizing primal basis of Eq. 6 by multigrid-preconditioned
+ * CG, S_PiPi and its Cholesky factor.  The problem must outlive the handle. */
+int ietidp_setup(const iga_problem* prob, const ietidp_options* opt, void* stream,
+                 ietidp_handle** out);
+
+int ietidp_info_get(const ietidp_handle* h, ietidp_info* info);
+/* Per-patch offsets into a torn vector: `offsets` has npatch+1 entries. */
+int ietidp_patch_offsets(const ietidp_handle* h, long long* offsets);
+
+/* Solve K~ u + B^T lambda = f~, B u = 0 (Eq. 2) through the dual problem
+ * F lambda = d of Eq. 4: d = B K~^{-1} f~, dual PCG with the scaled
+ * Dirichlet preconditioner, u = K~^{-1}(f~ - B^T lambda).
+ * f: device load vector in patch layout, or NULL for the assembled load;
+ * u_out: device, n_torn doubles.  `stats` may be NULL. */
+int ietidp_solve(ietidp_handle* h, const double* f, double* u_out, ietidp_stats* stats);
+
+/* Same as ietidp_solve with HOST buffers: copies f to the device, solves and
+ * copies u back, all on the handle's stream (f may be NULL as above). */
+int ietidp_solve_host(ietidp_handle* h, const double* f_host, double* u_host,
+                      ietidp_stats* stats);
+
+/* Apply `ncycles` V-cycles (Sec. 4 multigrid) to every patch's Neumann
+ * hierarchy in one batched launch each: x <- x + V(b - A x), with b and x
+ * device vectors in patch layout.  Used to measure V-cycle throughput. */
+int ietidp_vcycles(ietidp_handle* h, const double* b, double* x, int ncycles);
+
+/* Helpers exposed for testing the building blocks against the oracle:
+ *  - ietidp_apply_K: y = K x per patch (Dirichlet rows/cols removed);
+ *  - ietidp_apply_F: q = F p on the multipliers (device, n_lambda);
+ *  - ietidp_apply_precond: z = M_sD^{-1} r;
+ *  - ietidp_apply_Ktilde_inv: u = K~^{-1} g (patch layout);
+ *  - ietidp_get_primal_basis: Phi^(k) of patch k, column-major, its full
+ *    tensor grid x n_Pi^(k), into a device buffer; returns n_Pi^(k) in *ncols;
+ *  - ietidp_get_spp: S_PiPi (host, n_primal^2, row-major). */
+int ietidp_apply_K(ietidp_handle* h, const double* x, double* y);
+int ietidp_apply_F(ietidp_handle* h, const double* p, double* q);
+int ietidp_apply_precond(ietidp_handle* h, const double* r, double* z);
+int ietidp_apply_Ktilde_inv(ietidp_handle* h, const double* g, double* u);
+int ietidp_get_primal_basis(ietidp_handle* h, int patch, double* phi, int* ncols);
+int ietidp_get_spp(ietidp_handle* h, double* spp_host);
+
+int ietidp_destroy(ietidp_handle* h);
+
+const char* ietidp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IETIDP_H */

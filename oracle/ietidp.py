@@ -28,7 +28,9 @@ each row), local part of the jump operator B.
   1/2 w'Kw - w'g on ker C (Eq. 7).  D-D: the saddle LU.  MG-MG: CG on K with
   right-hand side P^T g, P = I - phi C, V-cycle preconditioner, stopped at
   relative residual tol_inner; then w = P z (Sec. 3.2: unconstrained solve
-  followed by the energy-minimizing projection).
+  followed by the energy-minimizing projection).  On patches without
+  Dirichlet sides the right-hand side is first made exactly orthogonal to the
+  constants (the kernel of K), which it is in exact arithmetic.
 * F = B K~^{-1} B^T, d = B K~^{-1} f (Eq. 4); scaled Dirichlet preconditioner
   M_sD^{-1} = B_D S B_D^T with S = K_BB - K_BI K_II^{-1} K_IB; K_II^{-1} exact
   (D-D) or two V-cycles (MG-MG, Sec. 4).
@@ -337,6 +339,11 @@ class IETIDP:
             rhs = np.concatenate([g, np.zeros(npi)])
             return self.kkt[k].solve(rhs)[: len(g)]
         b = g - C.T @ (phi.T @ g) if npi else g.copy()
+        if self.floating[k]:
+            # ker K = constants; P^T g is orthogonal to them only up to the
+            # accuracy of phi, so remove that component (exact in exact
+            # arithmetic) to keep CG on the semidefinite K consistent.
+            b -= b.mean()
         z, it, ok = multigrid.pcg(lambda x: self.K[k] @ x, b, self.mgN[k].vcycle,
                                   self.o.tol_inner, self.o.maxit_inner)
         self.stats.neumann_its.append(it)

@@ -1,0 +1,110 @@
+// Shared device-side data model of the IETI-DP library.
+//
+// Every patch keeps its spline space on the full tensor grid of
+// m_r = n_r + p_r functions per direction (first direction fastest).
+// Boundary conditions are side masks: side 2r is xi_r = 0, side 2r+1 is
+// xi_r = 1; a masked side's functions are removed from the operator (their
+// rows are skipped, their vector entries stay 0).
+//
+// Banded stiffness storage ("color-major ELL"): for a level with n functions
+// and stencil size S = prod_r (2 p_r + 1), values[o * n + s] holds
+// K(i, i + offset(o)) where s is the storage position of row i.  Rows are
+// stored color by color (color c = sum_r (i_r mod (p_r+1)) * stride_r, the
+// multicolor Gauss-Seidel classes), and within a color in lexicographic order
+// of t_r = i_r / (p_r+1).  A warp working on one color therefore reads each
+// stencil diagonal with unit stride.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define IETI_MAXD 3
+#define IETI_MAXLEV 12
+#define IETI_MAXP 6
+
+struct LevelDesc {
+    int m[3];          // functions per direction (1 for unused directions)
+    int n;             // m0*m1*m2
+    int S;             // stencil size
+    int refined[3];    // 1 if this level halves the elements of level l-1 along r
+    long long koff;    // offset of this level's values in the value arrays
+    int voff;          // offset of this level's vectors in a slot's level block
+    // 1D tables (offsets into the table pools), valid for level l > 0:
+    //  restriction (column form): for coarse index I of level l-1,
+    //    itab[rs + I] = first fine index, tab[rw + I*W + t] = P(first+t, I)
+    //  prolongation (row form): for fine index i of level l,
+    //    itab[ps + i] = first coarse index, tab[pw + i*W + t] = P(i, first+t)
+    int rs[3], rw[3], ps[3], pw[3];
+    // parameter-domain mass band: tab[mw + i*(2p+1) + (o+p)] = M(i, i+o)
+    int mw[3];
+};
+
+struct PatchDesc {
+    int dim;
+    int p[3];
+    int nelem[3];
+    int L;               // levels (0 = coarsest, L-1 = fine)
+    int dmask;           // sides on the Dirichlet boundary
+    int floating;        // 1 if dmask == 0
+    long long toff;      // offset of this patch in torn vectors
+    int n;               // fine functions
+    int nlvec;           // sum over levels of n_l
+    long long a0off[2];  // coarsest inverse (n0 x n0), hierarchy 0 (Neumann) / 1 (Dirichlet)
+    int npi;             // primal constraint rows of this patch
+    int crow0;           // first global C row of this patch
+    long long phioff;    // Phi (n x npi, column-major)
+    LevelDesc lev[IETI_MAXLEV];
+};
+
+// ---------------------------------------------------------------------------
+// index helpers
+// ---------------------------------------------------------------------------
+__host__ __device__ inline int ieti_cnt(int m, int p, int c) { return (m - c + p) / (p + 1); }
+
+__host__ __device__ inline int ieti_prefix(int m, int p, int c) {
+    int s = 0;
+    for (int k = 0; k < c; ++k) s += ieti_cnt(m, p, k);
+    return s;
+}
+
+// storage offset of color (c0,c1,c2)
+__host__ __device__ inline int ieti_color_off(const int* m, const int* p, int c0, int c1, int c2) {
+    return m[0] * m[1] * ieti_prefix(m[2], p[2], c2) +
+           ieti_cnt(m[2], p[2], c2) * (m[0] * ieti_prefix(m[1], p[1], c1) +
+                                       ieti_cnt(m[1], p[1], c1) * ieti_prefix(m[0], p[0], c0));
+}
+
+// storage position of natural row (i0,i1,i2)
+__host__ __device__ inline int ieti_store_pos(const int* m, const int* p, int i0, int i1, int i2) {
+    int c0 = i0 % (p[0] + 1), c1 = i1 % (p[1] + 1), c2 = i2 % (p[2] + 1);
+    int t0 = i0 / (p[0] + 1), t1 = i1 / (p[1] + 1), t2 = i2 / (p[2] + 1);
+    return ieti_color_off(m, p, c0, c1, c2) +
+           t0 + ieti_cnt(m[0], p[0], c0) * (t1 + ieti_cnt(m[1], p[1], c1) * t2);
+}
+
+__host__ __device__ inline int ieti_ncolors(const int* p) { return (p[0] + 1) * (p[1] + 1) * (p[2] + 1); }
+
+__host__ __device__ inline bool ieti_masked(int mask, const int* m, int i0, int i1, int i2) {
+    if ((mask & 1) && i0 == 0) return true;
+    if ((mask & 2) && i0 == m[0] - 1) return true;
+    if ((mask & 4) && i1 == 0) return true;
+    if ((mask & 8) && i1 == m[1] - 1) return true;
+    if ((mask & 16) && i2 == 0) return true;
+    if ((mask & 32) && i2 == m[2] - 1) return true;
+    return false;
+}
+
+__host__ __device__ inline bool ieti_on_boundary(const int* m, int dim, int i0, int i1, int i2) {
+    if (i0 == 0 || i0 == m[0] - 1) return true;
+    if (i1 == 0 || i1 == m[1] - 1) return true;
+    if (dim == 3 && (i2 == 0 || i2 == m[2] - 1)) return true;
+    return false;
+}
+
+// error flags written by kernels (bit field in a device int)
+#define IETI_FLAG_NOT_CONVERGED 1
+#define IETI_FLAG_BREAKDOWN     2
+#define IETI_FLAG_NONFINITE     4
+#define IETI_FLAG_TABLE         8
+#define IETI_FLAG_NOT_SPD      16
+
+#define IETI_CUDA_CHECK(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) return e_; } while (0)

@@ -1,0 +1,150 @@
+// Launch wrappers shared by the host orchestration and the kernel files.
+#pragma once
+#include "common.cuh"
+
+// ---- setup data ------------------------------------------------------------
+struct AsmTables {          // per (patch, direction) assembly tables
+    int nq;                 // Gauss points along the direction (n*(p+1))
+    long long qoff;         // offset into qx / qw (nq entries)
+    long long boff;         // offset into B / D ((p+1) values per point)
+};
+
+struct SetupArgs {
+    int npatch, dim;
+    const PatchDesc* pd;         // device
+    const double* geo;           // device, per patch: kind, lo[3], hi[3] (7 doubles)
+    const AsmTables* at;         // device, npatch*3
+    double* qx; double* qw; double* Bv; double* Dv;
+    const long long* qpoff;      // device, per patch: offset of its Gauss points (npatch+1)
+    double* Gm;                  // 6 doubles per Gauss point
+    double* Fw;                  // 1 double per Gauss point
+    int rhs_kind;
+    const double* modes;         // nmodes*3 (a, k, l)
+    int nmodes;
+    const double* quad_values;   // IGA_RHS_QUAD
+    const long long* rowoff;     // device, per patch: prefix of fine n (npatch+1)
+    double* K64;                 // value pool
+    double* f;                   // torn load vector
+    double* tab; int* itab;      // 1D table pools
+    int* flags;
+};
+
+cudaError_t launch_assembly(const SetupArgs& a, long long total_qp, long long total_rows,
+                            int max_S, cudaStream_t st);
+
+struct TableJob { int patch, level, r; };
+cudaError_t launch_tables(const SetupArgs& a, const TableJob* jobs_dev, int njobs, int max_m,
+                          cudaStream_t st);
+cudaError_t launch_mass_tables(const SetupArgs& a, const TableJob* jobs_dev, int njobs, cudaStream_t st);
+
+// Galerkin coarsening of all patches whose fine level minus `depth` exists.
+cudaError_t launch_galerkin(const PatchDesc* pd, const int* patch_list, int npl,
+                            int depth, int max_rows, int max_S, double* K64, const double* tab,
+                            const int* itab, cudaStream_t st);
+
+// Dense inverses of the coarsest operators: job = patch*2 + kind.
+cudaError_t launch_coarse_inverse(const PatchDesc* pd, int npatch, const double* K64,
+                                  const double* tab, double alpha, double* A0inv64,
+                                  float* A0inv32, double* work, int max_n0, int* flags,
+                                  cudaStream_t st);
+
+// Constraint weights: entries of C rows (vertex = 1, edge/face = normalized
+// integrals of the tangential basis functions).
+cudaError_t launch_cweights(const PatchDesc* pd, int nrows, const int* crow_ptr,
+                            const int* crow_patch, const int* crow_tang, const int* c_idx,
+                            double* c_w, cudaStream_t st);
+
+cudaError_t launch_to_f32(const double* src, float* dst, long long n, cudaStream_t st);
+
+// Dense SPD: Cholesky factor and inverse of the lower factor, one CTA.
+cudaError_t launch_chol_linv(const double* A, int n, double* Linv, double* work, int* flags,
+                             cudaStream_t st);
+
+// ---- solve data --------------------------------------------------------------
+struct SlotDesc {
+    int patch;
+    int kind;            // 0: Neumann hierarchy, 1: Dirichlet hierarchy
+    int row;             // basis mode: global C row
+    int pad;
+    long long cg;        // offset of the slot's FP64 vectors (5 n)
+    long long lv;        // offset of the slot's level vectors (3 nlvec)
+};
+
+enum SlotMode { MODE_NEUMANN = 0, MODE_BASIS = 1, MODE_SCHUR = 2, MODE_VCYCLE = 3 };
+
+struct SolveArgs {
+    const PatchDesc* pd;
+    const SlotDesc* slots;
+    int nslots;
+    int mode;
+    int mixed;                 // V-cycles in FP32
+    const double* K64;
+    const float* K32;
+    const double* tab;
+    const float* tabf;
+    const int* itab;
+    const double* A0inv64;
+    const float* A0inv32;
+    const int* crow_ptr;       // C rows: entries [crow_ptr[j], crow_ptr[j+1])
+    const int* c_idx;          // local function index
+    const double* c_w;         // weight
+    double* phi;               // primal basis pool
+    double* cg;                // FP64 vector pool
+    void* lv;                  // level vector pool (double or float)
+    const double* in;          // torn input
+    double* out;               // torn output
+    const double* rpi_loc;     // per C row: Phi^T g
+    const double* upi_loc;     // per C row: (A u_Pi)
+    int* its;                  // per slot iterations
+    int* flags;
+    double tol;
+    int maxit;
+    int nu1, nu2;
+    double alpha;
+    int ncycles;               // Schur: V-cycles; V-cycle mode: cycles
+    long long* vstats;         // [0] V-cycles, [1] V-cycle fine dofs (atomically added)
+};
+
+cudaError_t launch_solve(const SolveArgs& a, int threads, cudaStream_t st);
+
+// ---- dual / primal helpers ---------------------------------------------------
+struct DualArgs {
+    int nlam;
+    const long long* la; const long long* lb;   // torn indices of the two copies
+    const int* ma; const int* mb;               // multiplicities
+    int nie;                                    // interface torn entries
+    const long long* ie_idx; const int* ie_mult;
+    const int* ie_ptr; const int* ie_lam; const signed char* ie_sgn;
+};
+
+cudaError_t launch_bt(const DualArgs& d, const double* lam, double* torn, int scaled, cudaStream_t st);
+cudaError_t launch_b(const DualArgs& d, const double* torn, double* q, int scaled, cudaStream_t st);
+cudaError_t launch_jump_scale(const DualArgs& d, const double* torn, double* out2, cudaStream_t st);
+
+cudaError_t launch_primal_restrict(const PatchDesc* pd, int nrows, const int* crow_patch,
+                                   const int* crow_local, const double* phi, const double* g,
+                                   double* rpi_loc, cudaStream_t st);
+cudaError_t launch_coarse_solve(int npi, int nrows, const int* crow_glob, const int* gptr,
+                                const int* glist, const double* Linv, const double* rpi_loc,
+                                double* upi, double* upi_loc, cudaStream_t st);
+cudaError_t launch_spp_local(const PatchDesc* pd, int nrows, const int* crow_patch,
+                             const int* crow_local, const double* phi, const double* K64,
+                             double* work, long long work_stride, double* sloc,
+                             const long long* sloc_off, cudaStream_t st);
+cudaError_t launch_spp_assemble(int npatch, const PatchDesc* pd, const int* crow_glob,
+                                const double* sloc, const long long* sloc_off, double* S,
+                                int npi, cudaStream_t st);
+
+// outer PCG (one CTA): state = [rz, pq, alpha, beta, rr, nd, ...]
+cudaError_t launch_outer_init(int n, const double* d, double* lam, double* r, double* state,
+                              cudaStream_t st);
+cudaError_t launch_outer_first(int n, const double* r, const double* z, double* p, double* state,
+                               cudaStream_t st);
+cudaError_t launch_outer_step1(int n, const double* p, const double* q, double* lam, double* r,
+                               double* state, double* hist, int it, cudaStream_t st);
+cudaError_t launch_outer_step2(int n, const double* r, const double* z, double* p, double* state,
+                               double* hist, int it, cudaStream_t st);
+cudaError_t launch_axpy_torn(long long n, const double* a, double s, const double* b,
+                             double* out, cudaStream_t st);
+cudaError_t launch_apply_K(const PatchDesc* pd, int npatch, const double* K64, const double* x,
+                           double* y, cudaStream_t st);
