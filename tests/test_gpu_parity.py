@@ -145,7 +145,7 @@ def test_host_buffers_equal_device(api):
 
 
 def test_vcycles_reduce_residual(api):
-    dom = DOMS["annulus3x3"]()
+    dom = DOMS["square_rq"]()
     prob = api.Problem(dom)
     sol = api.Solver(prob)
     f = prob.load()
