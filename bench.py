@@ -1,0 +1,384 @@
+"""Benchmark of the GB300 inexact IETI-DP solver (MG-MG variant).
+
+Workload: 2D Poisson on the quarter annulus (radii 1 and 2, exact NURBS map)
+split into 6x6 patches, p = 3, 64x64 elements per patch (148,225 free dofs,
+161,604 torn dofs, 3,900 multipliers, 85 primal dofs), vertex and
+edge-average primal constraints, f from the manufactured solution
+u = sin(pi x) sin(pi y) (r-1)(2-r).  Synthetic, deterministic input.
+
+A step is one complete ``ietidp_solve`` (d = B K~^{-1} f, the dual PCG to
+1e-10 with the scaled Dirichlet preconditioner, recovery of u) with the
+load vector resident in HBM; setup is timed separately.  The headline is the
+mixed path (FP32 V-cycles under FP64 CG); the FP64 path is timed beside it.
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank runs an independent replica (the solver has no
+cross-GPU exchange step); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1705_04531_gb300 import workloads as W  # noqa: E402
+
+WORKLOAD = "annulus6x6_p3_n64"
+METRIC = "IETI-DP solves/sec (mixed FP32 V-cycles / FP64 CG, rel err <= 1e-8)"
+UNIT = "solves/s"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--vcycle-reps", type=int, default=50)
+    return ap.parse_args()
+
+
+def workload(name):
+    return W.by_name(name)
+
+
+# ---------------------------------------------------------------------------
+# algorithmic bytes of the batched Neumann solver kernel (per CG iteration of
+# one patch): V-cycle at nu1 = nu2 = 2 + FP64 stiffness SpMV + CG vectors
+# ---------------------------------------------------------------------------
+def levels(nelem, degree, cmin=4):
+    sched = [tuple(nelem)]
+    while True:
+        cur = sched[-1]
+        nxt = tuple(n // 2 if (n > cmin and n % 2 == 0) else n for n in cur)
+        if nxt == cur:
+            break
+        sched.append(nxt)
+    sched = sched[::-1]
+    out = []
+    for ne in sched:
+        n = int(np.prod([a + p for a, p in zip(ne, degree)]))
+        S = int(np.prod([2 * p + 1 for p in degree]))
+        out.append((n, S))
+    return out
+
+
+def bytes_per_iteration(nelem, degree, sv, nu=4):
+    lv = levels(nelem, degree)
+    b = 0
+    for l in range(1, len(lv)):
+        n, S = lv[l]
+        nc = lv[l - 1][0]
+        b += (nu + 1) * (S * n * sv + 3 * n * sv)       # sweeps + residual: values, x, b, x/r write
+        b += 3 * n * sv + 2 * nc * sv                   # restriction and prolongation
+    n0 = lv[0][0]
+    b += n0 * n0 * sv + 2 * n0 * sv                     # coarsest dense solve
+    n, S = lv[-1]
+    b += S * n * 8 + 2 * n * 8                          # FP64 SpMV q = K p
+    b += 12 * n * 8 + n * (8 + sv) * 2                  # CG vector updates, dots, casts
+    return b
+
+
+def vcycle_bytes(nelem, degree, sv, nu=4):
+    lv = levels(nelem, degree)
+    b = 0
+    for l in range(1, len(lv)):
+        n, S = lv[l]
+        nc = lv[l - 1][0]
+        b += (nu + 1) * (S * n * sv + 3 * n * sv) + 3 * n * sv + 2 * nc * sv
+    n0 = lv[0][0]
+    return b + n0 * n0 * sv + 2 * n0 * sv
+
+
+# ---------------------------------------------------------------------------
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            if len(r) >= 9:
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+def oracle_run(dom, budget_s=30.0):
+    """The oracle (D-D variant: sparse LU local solves) timed on the host on
+    complete solves of the same workload (setup excluded)."""
+    from oracle import ietidp as O
+    t0 = time.perf_counter()
+    s = O.IETIDP(dom, O.Options(mode="direct"))
+    t_setup = time.perf_counter() - t0
+    times = []
+    u = None
+    while True:
+        s.stats = O.Stats()
+        t = time.perf_counter()
+        u = s.solve()
+        times.append(time.perf_counter() - t)
+        if sum(times) > budget_s or len(times) >= 3:
+            break
+    return {"u": u, "times": times, "setup_s": t_setup, "outer_it": s.stats.outer_it}
+
+
+def relerr(got, ref):
+    return float(np.sqrt(sum(np.sum((a - b) ** 2) for a, b in zip(got, ref)) /
+                         sum(np.sum(b ** 2) for b in ref)))
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    dom = workload(args.workload)
+    from oracle import ietidp as O
+    s = O.IETIDP(dom, O.Options(mode="direct"))
+    for _ in range(max(0, min(args.warmup, 1))):
+        s.stats = O.Stats()
+        s.solve()
+    times = []
+    for _ in range(args.steps):
+        s.stats = O.Stats()
+        t = time.perf_counter()
+        s.solve()
+        times.append(time.perf_counter() - t)
+    v = len(times) / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "variant": "D-D (CPU oracle)"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} complete solves of {args.workload}, setup excluded"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def time_path(api, torch, prob, prec, args, flush, stream):
+    t0 = time.perf_counter()
+    sol = api.Solver(prob, precision=prec)
+    torch.cuda.synchronize()
+    setup_ms = 1e3 * (time.perf_counter() - t0)
+    f = prob.load()
+    u = torch.empty(sol.n_torn, dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        sol.solve(f, u)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stats = []
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        _, st = sol.solve(f, u)
+        ev[k][1].record(stream)
+        stats.append(st)
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    return sol, u, ms, stats, setup_ms
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1705_04531_gb300 import build
+    build.build()
+    from paper_1705_04531_gb300 import ietidp as api
+
+    dom = workload(args.workload)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    t0 = time.perf_counter()
+    prob = api.Problem(dom)
+    torch.cuda.synchronize()
+    assemble_ms = 1e3 * (time.perf_counter() - t0)
+
+    # FP64 path first (the comparison), then the mixed path (headline)
+    sol64, u64, ms64, st64, setup64 = time_path(api, torch, prob, "fp64", args, flush, stream)
+    u64h = sol64.split(u64)
+    sol64.close()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        sol, u, ms, sts, setup_ms = time_path(api, torch, prob, "mixed", args, flush, stream)
+    torch.cuda.synchronize()
+    tot = sum(ms)
+    if dist:
+        t = torch.tensor([tot], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot = float(t.item())
+    value = world * args.steps / (tot / 1e3)
+    uh = sol.split(u)
+
+    # V-cycle throughput: one batched V-cycle over all 36 Neumann hierarchies per launch
+    f = prob.load()
+    x = torch.zeros_like(f)
+    for _ in range(3):
+        sol.vcycles(f, x, 1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.vcycle_reps):
+        sol.vcycles(f, x, 1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    vc_ms = e0.elapsed_time(e1) / args.vcycle_reps
+    nfine = sum(dom.patch_ndof(k) for k in range(dom.npatch))
+    vcycle_dofs_s = nfine / (vc_ms / 1e3)
+
+    # e2e through the C ABI with host buffers (pinned), copies inside the timed region
+    fh = torch.empty(sol.n_torn, dtype=torch.float64).pin_memory()
+    fh.copy_(f.cpu())
+    uh_host = torch.empty(sol.n_torn, dtype=torch.float64).pin_memory()
+    fnp, unp = fh.numpy(), uh_host.numpy()
+    sol.solve_host(fnp, unp)
+    torch.cuda.synchronize()
+    e2e_t = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        sol.solve_host(fnp, unp)
+        e2e_t.append(time.perf_counter() - t)
+    e2e_val = world * len(e2e_t) / sum(e2e_t)
+
+    if rank != 0:
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    # roofline of the dominant kernel: the batched Neumann solver (k_solve<float>)
+    p = dom.patch_degree(0)
+    ne = dom.patch_nelem(0)
+    iters = sum(s["inner_its"] for s in sts)
+    nlaunch = sum(s["neumann_launches"] for s in sts)
+    kms = sum(s["neumann_ms"] for s in sts)
+    bpi = bytes_per_iteration(ne, p, 4)
+    alg_bytes_per_launch = iters * bpi / max(1, nlaunch)
+    achieved = alg_bytes_per_launch / (kms / max(1, nlaunch) / 1e3) / 1e9
+    peak, peak_kind = peaks()
+    traffic = None
+    tp = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tp):
+        with open(tp) as fh_:
+            traffic = json.load(fh_).get(args.workload)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 V-cycle + f64 CG",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "patches": dom.npatch, "degree": 3, "elements_per_patch": "64x64",
+                   "free_dofs": 148225, "torn_dofs": sol.n_torn, "multipliers": sol.info.n_lambda,
+                   "primal": sol.info.n_primal, "precision": "mixed", "tol_outer": 1e-10,
+                   "l2": f"{L2_FLUSH_BYTES >> 20} MiB buffer written between timed steps",
+                   "replicas": world},
+        "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
+        "outer_it": sts[-1]["outer_it"], "inner_it_avg": sts[-1]["inner_it_avg"],
+        "kappa": sts[-1]["kappa"],
+        "setup_ms": setup_ms, "assemble_ms": assemble_ms,
+        "fp64": {"value": world * args.steps / (sum(ms64) / 1e3), "ms_per_step": sum(ms64) / args.steps,
+                 "p50_ms": float(np.percentile(ms64, 50)), "p99_ms": float(np.percentile(ms64, 99)),
+                 "outer_it": st64[-1]["outer_it"], "inner_it_avg": st64[-1]["inner_it_avg"],
+                 "setup_ms": setup64},
+        "mixed_over_fp64": (sum(ms64) / sum(ms)),
+        "vcycle_dofs_per_s": vcycle_dofs_s, "vcycle_ms": vc_ms,
+        "roofline": {"bound": "hbm", "kernel": "k_solve<float> (batched Neumann PCG + V-cycles)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_kind": peak_kind, "traffic": traffic,
+                     "alg_bytes_per_launch": alg_bytes_per_launch,
+                     "launch_ms": kms / max(1, nlaunch)},
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 8 * sol.n_torn,
+                "d2h_bytes_per_step": 8 * sol.n_torn},
+        "gpu_launches": int(sum(s["launches"] for s in sts)),
+        "clocks": clk.summary(),
+    }
+    if not args.no_cpu_baseline:
+        orc = oracle_run(dom)
+        ref = orc["u"]
+        line["rel_err_mixed"] = relerr(uh, ref)
+        line["rel_err_fp64"] = relerr(u64h, ref)
+        v = len(orc["times"]) / sum(orc["times"])
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"{len(orc['times'])} complete D-D solves of {args.workload} "
+                                          f"(sparse LU local solves), setup excluded",
+                                "outer_it": orc["outer_it"]}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -149,6 +149,10 @@ typedef struct {
     long long vcycles;        /* V-cycles executed (all patches)               */
     long long vcycle_dofs;    /* sum over V-cycles of fine-level dofs          */
     double t_setup_ms, t_solve_ms;
+    long long launches;       /* kernels launched by this solve                */
+    int    neumann_launches;  /* launches of the batched Neumann solver kernel */
+    double neumann_ms;        /* their total device time (CUDA events)         */
+    long long inner_its;      /* CG iterations summed over all Neumann slots   */
 } ietidp_stats;
 
 typedef struct {

@@ -153,6 +153,9 @@ struct ietidp_handle {
     double *state = nullptr, *hist = nullptr, *scal = nullptr;
     double* h_pinned = nullptr;
     double t_setup_ms = 0;
+    long long launches = 0;         // kernels launched since the last reset
+    std::vector<cudaEvent_t> ev;    // Neumann solver launch brackets (pairs)
+    int nev_used = 0;
     double basis_it_avg = 0;
     int basis_it_max = 0;
     int n_floating = 0;
@@ -512,7 +515,14 @@ static int run_solve(ietidp_handle* h, int mode, const SlotDesc* slots, int nslo
     a.alpha = h->opt.alpha_reg;
     a.ncycles = h->opt.dirichlet_vcycles;
     a.vstats = vst;
+    bool timed = mode == MODE_NEUMANN && h->nev_used + 2 <= (int)h->ev.size();
+    if (timed) cudaEventRecord(h->ev[h->nev_used], h->st);
     cudaError_t e = launch_solve(a, 512, h->st);
+    if (timed) {
+        cudaEventRecord(h->ev[h->nev_used + 1], h->st);
+        h->nev_used += 2;
+    }
+    h->launches += 1;
     if (e != cudaSuccess) return fail(IETIDP_E_CUDA, std::string("solve kernel: ") + cudaGetErrorString(e));
     return IETIDP_OK;
 }
@@ -999,6 +1009,8 @@ extern "C" int ietidp_setup(const iga_problem* P, const ietidp_options* opt_in, 
     CKH(h->mem.alloc(&h->hist, 2 * (opt.maxit_outer + 2)));
     CKH(h->mem.alloc(&h->scal, 4));
     CUH(cudaMallocHost(&h->h_pinned, sizeof(double) * 16));
+    h->ev.resize(2 * (2 * opt.maxit_outer + 8));
+    for (auto& ev : h->ev) CUH(cudaEventCreate(&ev));
     CUH(cudaStreamSynchronize(st));
     auto t1 = std::chrono::steady_clock::now();
     h->t_setup_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
@@ -1013,6 +1025,7 @@ extern "C" int ietidp_setup(const iga_problem* P, const ietidp_options* opt_in, 
 // ---------------------------------------------------------------------------
 static int ktilde_inv(ietidp_handle* h, const double* g, double* u) {
     cudaStream_t st = h->st;
+    h->launches += (h->nrows > 0) + (h->npi > 0);
     cudaError_t e = launch_primal_restrict(h->d_pd, h->nrows, h->crow_patch, h->crow_local, h->phi, g, h->rloc, st);
     if (e == cudaSuccess)
         e = launch_coarse_solve(h->npi, h->nrows, h->crow_glob, h->gptr, h->glist, h->Linv, h->rloc, h->upi, h->uloc, st);
@@ -1022,6 +1035,7 @@ static int ktilde_inv(ietidp_handle* h, const double* g, double* u) {
 }
 
 static int apply_F(ietidp_handle* h, const double* pv, double* qv) {
+    h->launches += 2;
     cudaError_t e = launch_bt(h->dual, pv, h->gF, 0, h->st);
     if (e != cudaSuccess) return fail(IETIDP_E_CUDA, cudaGetErrorString(e));
     CHK(ktilde_inv(h, h->gF, h->uF));
@@ -1031,6 +1045,7 @@ static int apply_F(ietidp_handle* h, const double* pv, double* qv) {
 }
 
 static int apply_M(ietidp_handle* h, const double* rv, double* zv) {
+    h->launches += 2;
     cudaError_t e = launch_bt(h->dual, rv, h->vS, 1, h->st);
     if (e != cudaSuccess) return fail(IETIDP_E_CUDA, cudaGetErrorString(e));
     CHK(run_solve(h, MODE_SCHUR, h->d_slots_patch, h->nslot_patch, h->vS, h->wS, 0.0, 0, h->vst));
@@ -1095,6 +1110,8 @@ extern "C" int ietidp_solve(ietidp_handle* h, const double* f, double* u_out, ie
     CU(cudaMemsetAsync(h->vst, 0, sizeof(long long) * 8, st));
     ietidp_stats S;
     std::memset(&S, 0, sizeof(S));
+    h->launches = 0;
+    h->nev_used = 0;
     // u0 = K~^{-1} f
     CHK(ktilde_inv(h, f, u_out));
     int it = 0;
@@ -1104,6 +1121,7 @@ extern "C" int ietidp_solve(ietidp_handle* h, const double* f, double* u_out, ie
         cudaError_t e = launch_b(h->dual, u_out, h->d, 0, st);
         if (e == cudaSuccess) e = launch_jump_scale(h->dual, u_out, h->scal, st);
         if (e == cudaSuccess) e = launch_outer_init(h->nlam, h->d, h->lam, h->r, h->state, st);
+        h->launches += 3;
         if (e != cudaSuccess) return fail(IETIDP_E_CUDA, cudaGetErrorString(e));
         CU(cudaMemcpyAsync(h->h_pinned, h->state + 5, sizeof(double), cudaMemcpyDeviceToHost, st));
         CU(cudaMemcpyAsync(h->h_pinned + 1, h->scal, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -1117,11 +1135,13 @@ extern "C" int ietidp_solve(ietidp_handle* h, const double* f, double* u_out, ie
             conv = false;
             CHK(apply_M(h, h->r, h->z));
             e = launch_outer_first(h->nlam, h->r, h->z, h->p, h->state, st);
+            h->launches += 1;
             if (e != cudaSuccess) return fail(IETIDP_E_CUDA, cudaGetErrorString(e));
             double thr2 = tol * tol * dd;
             for (it = 1; it <= h->opt.maxit_outer; ++it) {
                 CHK(apply_F(h, h->p, h->q));
                 e = launch_outer_step1(h->nlam, h->p, h->q, h->lam, h->r, h->state, h->hist, it - 1, st);
+                h->launches += 1;
                 if (e != cudaSuccess) return fail(IETIDP_E_CUDA, cudaGetErrorString(e));
                 CU(cudaMemcpyAsync(h->h_pinned, h->state + 4, sizeof(double), cudaMemcpyDeviceToHost, st));
                 CU(cudaStreamSynchronize(st));
@@ -1134,6 +1154,7 @@ extern "C" int ietidp_solve(ietidp_handle* h, const double* f, double* u_out, ie
                 }
                 CHK(apply_M(h, h->r, h->z));
                 e = launch_outer_step2(h->nlam, h->r, h->z, h->p, h->state, h->hist, it - 1, st);
+                h->launches += 1;
                 if (e != cudaSuccess) return fail(IETIDP_E_CUDA, cudaGetErrorString(e));
             }
             if (!conv) it = h->opt.maxit_outer;
@@ -1147,6 +1168,7 @@ extern "C" int ietidp_solve(ietidp_handle* h, const double* f, double* u_out, ie
             // recovery: u = K~^{-1}(f - B^T lambda)
             e = launch_bt(h->dual, h->lam, h->tmp, 0, st);
             if (e == cudaSuccess) e = launch_axpy_torn(P->ntorn, f, -1.0, h->tmp, h->gR, st);
+            h->launches += 2;
             if (e != cudaSuccess) return fail(IETIDP_E_CUDA, cudaGetErrorString(e));
             CHK(ktilde_inv(h, h->gR, u_out));
         }
@@ -1165,6 +1187,18 @@ extern "C" int ietidp_solve(ietidp_handle* h, const double* f, double* u_out, ie
     S.basis_it_max = h->basis_it_max;
     S.t_setup_ms = h->t_setup_ms;
     S.t_solve_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    S.launches = h->launches;
+    S.neumann_launches = h->nev_used / 2;
+    for (int k = 0; k + 1 < h->nev_used; k += 2) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, h->ev[k], h->ev[k + 1]);
+        S.neumann_ms += ms;
+    }
+    S.inner_its = vs[2];
+    if (vs[4] > 0) {
+        S.inner_it_avg = (double)vs[2] / (double)vs[4];
+        S.inner_it_max = (int)vs[3];
+    }
     if (stats) *stats = S;
     if (fl & IETI_FLAG_BREAKDOWN) return fail(IETIDP_E_BREAKDOWN, "CG breakdown in a local solve");
     if (!S.converged) return fail(IETIDP_E_NOT_CONVERGED, "solver did not converge");
@@ -1262,6 +1296,7 @@ extern "C" int ietidp_destroy(ietidp_handle* h) {
     cudaStreamSynchronize(h->st);
     h->mem.release();
     if (h->h_pinned) cudaFreeHost(h->h_pinned);
+    for (auto& ev : h->ev) cudaEventDestroy(ev);
     delete h;
     return IETIDP_OK;
 }

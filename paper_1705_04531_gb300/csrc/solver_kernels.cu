@@ -575,6 +575,9 @@ __global__ void __launch_bounds__(512) k_solve(SolveArgs a) {
         if (a.vstats) {
             atomicAdd((unsigned long long*)&a.vstats[0], (unsigned long long)vcount);
             atomicAdd((unsigned long long*)&a.vstats[1], (unsigned long long)(vcount * n));
+            atomicAdd((unsigned long long*)&a.vstats[2], (unsigned long long)it);
+            atomicMax((unsigned long long*)&a.vstats[3], (unsigned long long)it);
+            if (nb2 > 0.0) atomicAdd((unsigned long long*)&a.vstats[4], 1ULL);
         }
     }
     // ---- epilogue ----------------------------------------------------------

@@ -66,7 +66,9 @@ class ietidp_stats(C.Structure):
                 ("inner_it_avg", C.c_double), ("inner_it_max", C.c_int),
                 ("basis_it_avg", C.c_double), ("basis_it_max", C.c_int),
                 ("vcycles", C.c_longlong), ("vcycle_dofs", C.c_longlong),
-                ("t_setup_ms", C.c_double), ("t_solve_ms", C.c_double)]
+                ("t_setup_ms", C.c_double), ("t_solve_ms", C.c_double),
+                ("launches", C.c_longlong), ("neumann_launches", C.c_int), ("neumann_ms", C.c_double),
+                ("inner_its", C.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
