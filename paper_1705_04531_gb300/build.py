@@ -14,7 +14,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libietidp.so")
-SOURCES = ["setup_kernels.cu", "solver_kernels.cu", "dual_kernels.cu", "ietidp_host.cu"]
+SOURCES = ["setup_kernels.cu", "solver_kernels.cu", "dual_kernels.cu", "ietidp_host.cu",
+           "solver_dispatch.cu", "solver_t_3d.cu"] + [
+    f"solver_t_{t}_2d_p{p}.cu" for t in ("f32", "f64") for p in (2, 3, 4)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 
@@ -45,7 +47,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and not stale():
         return LIB
     os.makedirs(OUT, exist_ok=True)
-    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+    with cf.ThreadPoolExecutor(max_workers=min(len(SOURCES), max(2, os.cpu_count() or 2))) as ex:
         objs = list(ex.map(_compile, SOURCES))
     tmp = LIB + ".tmp"
     cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]

@@ -110,6 +110,16 @@ struct iga_problem {
     double* f = nullptr;             // load (torn)
 };
 
+struct SlotGroup {        // slots served by one kernel specialisation
+    int dim, p0, p1, p2;
+    SlotDesc* d = nullptr;
+    int n = 0;
+    int its_off = 0;
+    size_t smem = 0;
+};
+
+constexpr size_t kSmemCap = 220 * 1024;   // dynamic shared memory per CTA
+
 struct ietidp_handle {
     const iga_problem* prob = nullptr;
     ietidp_options opt;
@@ -138,8 +148,11 @@ struct ietidp_handle {
     DualArgs dual{};
     int nlam = 0;
     // slots
-    SlotDesc* d_slots_patch = nullptr;   // one slot per patch (Neumann / Schur)
-    int nslot_patch = 0;
+    std::vector<SlotGroup> gpatch;       // one slot per patch (Neumann / Schur)
+    std::vector<SlotGroup> gbasis;       // one slot per primal row
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> join;
+    cudaEvent_t fork = nullptr;
     double* cg = nullptr;
     void* lv = nullptr;
     int* its = nullptr;
@@ -481,12 +494,23 @@ static std::vector<std::array<int, 3>> schedule(const int* nel, int d, int cmin)
     return s;
 }
 
-static int run_solve(ietidp_handle* h, int mode, const SlotDesc* slots, int nslots, const double* in, double* out,
-                     double tol, int maxit, long long* vst) {
+static int launch_group(ietidp_handle* h, SolveArgs a, const SlotGroup& g, cudaStream_t st) {
+    a.slots = g.d;
+    a.nslots = g.n;
+    a.its = h->its + g.its_off;
+    a.smem_bytes = g.smem;
+    cudaError_t e;
+    if (solve_variant_exists(g.dim, g.p0, g.p1, g.p2)) e = launch_solve_variant(a, g.dim, g.p0, g.p1, g.p2, 512, st);
+    else e = launch_solve(a, 512, st);
+    h->launches += 1;
+    if (e != cudaSuccess) return fail(IETIDP_E_CUDA, std::string("solve kernel: ") + cudaGetErrorString(e));
+    return IETIDP_OK;
+}
+
+static int run_solve(ietidp_handle* h, int mode, const std::vector<SlotGroup>& groups, const double* in,
+                     double* out, double tol, int maxit, long long* vst) {
     SolveArgs a{};
     a.pd = h->d_pd;
-    a.slots = slots;
-    a.nslots = nslots;
     a.mode = mode;
     a.mixed = h->opt.precision == IETIDP_PREC_MIXED;
     a.K64 = h->K64;
@@ -506,7 +530,6 @@ static int run_solve(ietidp_handle* h, int mode, const SlotDesc* slots, int nslo
     a.out = out;
     a.rpi_loc = h->rloc;
     a.upi_loc = h->uloc;
-    a.its = h->its;
     a.flags = h->flags;
     a.tol = tol;
     a.maxit = maxit;
@@ -517,13 +540,49 @@ static int run_solve(ietidp_handle* h, int mode, const SlotDesc* slots, int nslo
     a.vstats = vst;
     bool timed = mode == MODE_NEUMANN && h->nev_used + 2 <= (int)h->ev.size();
     if (timed) cudaEventRecord(h->ev[h->nev_used], h->st);
-    cudaError_t e = launch_solve(a, 512, h->st);
+    if (groups.size() == 1) {
+        CHK(launch_group(h, a, groups[0], h->st));
+    } else if (!groups.empty()) {
+        // groups of different specialisations run concurrently on side streams
+        CU(cudaEventRecord(h->fork, h->st));
+        for (size_t i = 0; i < groups.size(); ++i) {
+            cudaStream_t s = h->side[i % h->side.size()];
+            CU(cudaStreamWaitEvent(s, h->fork, 0));
+            CHK(launch_group(h, a, groups[i], s));
+        }
+        for (size_t i = 0; i < std::min(groups.size(), h->side.size()); ++i) {
+            CU(cudaEventRecord(h->join[i], h->side[i]));
+            CU(cudaStreamWaitEvent(h->st, h->join[i], 0));
+        }
+    }
     if (timed) {
         cudaEventRecord(h->ev[h->nev_used + 1], h->st);
         h->nev_used += 2;
     }
-    h->launches += 1;
-    if (e != cudaSuccess) return fail(IETIDP_E_CUDA, std::string("solve kernel: ") + cudaGetErrorString(e));
+    return IETIDP_OK;
+}
+
+static int make_groups(ietidp_handle* h, const std::vector<SlotDesc>& slots, std::vector<SlotGroup>& out,
+                       cudaStream_t st) {
+    bool mixed = h->opt.precision == IETIDP_PREC_MIXED;
+    std::map<std::tuple<int, int, int, int>, std::vector<SlotDesc>> by;
+    for (const SlotDesc& sd : slots) {
+        const PatchDesc& P = h->pd[sd.patch];
+        by[std::make_tuple(P.dim, P.p[0], P.p[1], P.p[2])].push_back(sd);
+    }
+    int off = 0;
+    for (auto& kv : by) {
+        SlotGroup g;
+        std::tie(g.dim, g.p0, g.p1, g.p2) = kv.first;
+        g.n = (int)kv.second.size();
+        g.its_off = off;
+        off += g.n;
+        size_t need = 0;
+        for (const SlotDesc& sd : kv.second) need = std::max(need, solve_smem_need(h->pd[sd.patch], mixed));
+        g.smem = std::min(need, kSmemCap);
+        CHK(h->mem.upload(&g.d, kv.second, st));
+        out.push_back(g);
+    }
     return IETIDP_OK;
 }
 
@@ -933,13 +992,24 @@ extern "C" int ietidp_setup(const iga_problem* P, const ietidp_options* opt_in, 
         h->lv = lvd;
     }
     CKH(h->mem.alloc(&h->its, nslots_max));
-    CKH(h->mem.upload(&h->d_slots_patch, sp, st));
-    h->nslot_patch = N;
-    SlotDesc* d_sb;
-    CKH(h->mem.upload(&d_sb, sb, st));
+    CKH(make_groups(h, sp, h->gpatch, st));
+    CKH(make_groups(h, sb, h->gbasis, st));
+    {
+        size_t ng = std::max(h->gpatch.size(), h->gbasis.size());
+        if (ng > 1) {
+            size_t ns = std::min<size_t>(ng, 8);
+            h->side.resize(ns);
+            h->join.resize(ns);
+            for (size_t i = 0; i < ns; ++i) {
+                CUH(cudaStreamCreateWithFlags(&h->side[i], cudaStreamNonBlocking));
+                CUH(cudaEventCreateWithFlags(&h->join[i], cudaEventDisableTiming));
+            }
+            CUH(cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming));
+        }
+    }
     // ---- primal basis (Eq. 6) ---------------------------------------------
     if (nslot_basis > 0) {
-        CHK(run_solve(h, MODE_BASIS, d_sb, nslot_basis, nullptr, nullptr, opt.tol_basis, opt.maxit_inner, h->vst + 8));
+        CHK(run_solve(h, MODE_BASIS, h->gbasis, nullptr, nullptr, opt.tol_basis, opt.maxit_inner, h->vst + 8));
         std::vector<int> its(nslot_basis);
         CUH(cudaMemcpyAsync(its.data(), h->its, sizeof(int) * nslot_basis, cudaMemcpyDeviceToHost, st));
         CUH(cudaStreamSynchronize(st));
@@ -1030,8 +1100,7 @@ static int ktilde_inv(ietidp_handle* h, const double* g, double* u) {
     if (e == cudaSuccess)
         e = launch_coarse_solve(h->npi, h->nrows, h->crow_glob, h->gptr, h->glist, h->Linv, h->rloc, h->upi, h->uloc, st);
     if (e != cudaSuccess) return fail(IETIDP_E_CUDA, std::string("primal: ") + cudaGetErrorString(e));
-    return run_solve(h, MODE_NEUMANN, h->d_slots_patch, h->nslot_patch, g, u, h->opt.tol_inner, h->opt.maxit_inner,
-                     h->vst);
+    return run_solve(h, MODE_NEUMANN, h->gpatch, g, u, h->opt.tol_inner, h->opt.maxit_inner, h->vst);
 }
 
 static int apply_F(ietidp_handle* h, const double* pv, double* qv) {
@@ -1048,7 +1117,7 @@ static int apply_M(ietidp_handle* h, const double* rv, double* zv) {
     h->launches += 2;
     cudaError_t e = launch_bt(h->dual, rv, h->vS, 1, h->st);
     if (e != cudaSuccess) return fail(IETIDP_E_CUDA, cudaGetErrorString(e));
-    CHK(run_solve(h, MODE_SCHUR, h->d_slots_patch, h->nslot_patch, h->vS, h->wS, 0.0, 0, h->vst));
+    CHK(run_solve(h, MODE_SCHUR, h->gpatch, h->vS, h->wS, 0.0, 0, h->vst));
     e = launch_b(h->dual, h->wS, zv, 1, h->st);
     if (e != cudaSuccess) return fail(IETIDP_E_CUDA, cudaGetErrorString(e));
     return IETIDP_OK;
@@ -1242,7 +1311,7 @@ extern "C" int ietidp_vcycles(ietidp_handle* h, const double* b, double* x, int 
     if (!h || !b || !x || ncycles < 0) return fail(IETIDP_E_INVALID_ARG, "bad argument");
     ietidp_options save = h->opt;
     h->opt.dirichlet_vcycles = ncycles;
-    int rc = run_solve(h, MODE_VCYCLE, h->d_slots_patch, h->nslot_patch, b, x, 0.0, 0, h->vst);
+    int rc = run_solve(h, MODE_VCYCLE, h->gpatch, b, x, 0.0, 0, h->vst);
     h->opt = save;
     return rc;
 }
@@ -1297,6 +1366,9 @@ extern "C" int ietidp_destroy(ietidp_handle* h) {
     h->mem.release();
     if (h->h_pinned) cudaFreeHost(h->h_pinned);
     for (auto& ev : h->ev) cudaEventDestroy(ev);
+    for (auto& sd : h->side) cudaStreamDestroy(sd);
+    for (auto& ev : h->join) cudaEventDestroy(ev);
+    if (h->fork) cudaEventDestroy(h->fork);
     delete h;
     return IETIDP_OK;
 }

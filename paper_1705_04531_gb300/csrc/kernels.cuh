@@ -103,9 +103,17 @@ struct SolveArgs {
     double alpha;
     int ncycles;               // Schur: V-cycles; V-cycle mode: cycles
     long long* vstats;         // [0] V-cycles, [1] V-cycle fine dofs (atomically added)
+    size_t smem_bytes;         // dynamic shared memory of the launch (specialised kernels)
 };
 
+// generic kernel (degrees known at run time only)
 cudaError_t launch_solve(const SolveArgs& a, int threads, cudaStream_t st);
+// kernel specialised for (dim, p0, p1, p2); cudaErrorNotSupported if none exists
+bool solve_variant_exists(int dim, int p0, int p1, int p2);
+cudaError_t launch_solve_variant(const SolveArgs& a, int dim, int p0, int p1, int p2, int threads,
+                                 cudaStream_t st);
+// shared memory a specialised launch would use for this patch (uncapped)
+size_t solve_smem_need(const PatchDesc& P, int mixed);
 
 // ---- dual / primal helpers ---------------------------------------------------
 struct DualArgs {

@@ -1,0 +1,709 @@
+// Batched local solver of inexact IETI-DP, specialised at compile time for
+// the patch dimension and spline degrees (stencil (2p_1+1)...(2p_d+1), Gauss-
+// Seidel colors (p_1+1)...(p_d+1)), so that every stencil loop is unrolled and
+// a row's loads are issued back to back.
+//
+// One CTA owns one local problem ("slot") for a whole launch.  Shared memory
+// holds, as far as the launch's budget allows: the patch descriptor, the
+// V-cycle vectors of every level, the coarsest-level inverse and the
+// matrices of the coarse levels (loaded once per launch, then reused by every
+// V-cycle of the CG).  The fine-level matrix streams from L2/HBM in
+// color-major order (unit-stride per stencil diagonal).
+//
+// Modes (Sec. 3): Neumann solve inside F and K~^{-1} (CG on K, V-cycle on K
+// or K + alpha M^, right-hand side P^T g, result P z + Phi u_Pi), primal basis
+// (Eq. 6 by the null-space method), scaled-Dirichlet Schur application
+// (two V-cycles on K_II), and a plain V-cycle iteration for benchmarking.
+#pragma once
+#include <math.h>
+#include "kernels.cuh"
+
+namespace ieti_t {
+
+constexpr int kMaxRows = 64;
+
+struct Red {
+    double v[32][4];
+};
+
+template <int K>
+__device__ __forceinline__ void cta_sum(double* val, Red& sh) {
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) val[k] += __shfl_xor_sync(0xffffffffu, val[k], o);
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k) sh.v[w][k] = val[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        double s = 0.0;
+        for (int i = 0; i < nw; ++i) s += sh.v[i][k];
+        val[k] = s;
+    }
+}
+
+__host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+// shared-memory plan of one slot for a dynamic budget B (same on host and device)
+struct Plan {
+    bool vec;       // V-cycle vectors in shared memory
+    bool a0;        // coarsest inverse in shared memory
+    int ls;         // matrices of levels 0..ls in shared memory (-1: none)
+    size_t a0_off, mat_off, used;
+};
+
+__host__ __device__ inline Plan make_plan(const PatchDesc& P, size_t tsize, size_t B) {
+    Plan pl;
+    size_t used = 0;
+    size_t vb = align16(3 * (size_t)P.nlvec * tsize);
+    pl.vec = vb <= B;
+    if (pl.vec) used += vb;
+    size_t ab = align16((size_t)P.lev[0].n * P.lev[0].n * tsize);
+    pl.a0 = used + ab <= B;
+    pl.a0_off = used;
+    if (pl.a0) used += ab;
+    pl.mat_off = used;
+    pl.ls = -1;
+    for (int l = 0; l < P.L - 1; ++l) {
+        size_t mb = (size_t)P.lev[l].n * P.lev[l].S * tsize;
+        if (used + mb > B) break;
+        used += mb;
+        pl.ls = l;
+    }
+    pl.used = used;
+    return pl;
+}
+
+// full shared-memory need of one slot (host side sizing)
+inline size_t smem_need(const PatchDesc& P, size_t tsize) {
+    size_t b = align16(3 * (size_t)P.nlvec * tsize) + align16((size_t)P.lev[0].n * P.lev[0].n * tsize);
+    for (int l = 0; l < P.L - 1; ++l) b += (size_t)P.lev[l].n * P.lev[l].S * tsize;
+    return b;
+}
+
+template <typename T, int D, int P0, int P1, int P2>
+struct VC {
+    static constexpr int W0 = 2 * P0 + 1, W1 = 2 * P1 + 1, W2 = 2 * P2 + 1;
+    static constexpr int C0 = P0 + 1, C1 = P1 + 1, C2 = P2 + 1, NC = C0 * C1 * C2;
+    static constexpr int R0 = P0 + 2, R1 = P1 + 2, R2 = D == 3 ? P2 + 2 : 1;
+
+    const PatchDesc* P;   // shared copy
+    int mask;
+    T alpha;
+    const T* Kg;          // global value pool
+    const T* Ks;          // shared matrices of levels 0..ls
+    int ls;
+    long long kbase;
+    const T* tab;
+    const int* itab;
+    const T* A0;
+    T* lvec;
+    int nlvec;
+
+    __device__ __forceinline__ const T* vals(int l) const {
+        return l <= ls ? Ks + (P->lev[l].koff - kbase) : Kg + P->lev[l].koff;
+    }
+    __device__ __forceinline__ T* X(int l) const { return lvec + P->lev[l].voff; }
+    __device__ __forceinline__ T* B(int l) const { return lvec + nlvec + P->lev[l].voff; }
+    __device__ __forceinline__ T* R(int l) const { return lvec + 2 * nlvec + P->lev[l].voff; }
+
+    // (A x)_i and the diagonal for row (i0,i1,i2) at storage position s
+    template <bool REG>
+    __device__ __forceinline__ T row(const T* v, int n, int s, const T* x, int m0, int m1, int m2, int i0, int i1,
+                                     int i2, const T* mt0, const T* mt1, const T* mt2, T* diag) const {
+        T acc = 0;
+        const int i = i0 + m0 * (i1 + m1 * i2);
+#pragma unroll
+        for (int o2 = -P2; o2 <= P2; ++o2) {
+            const bool v2 = (unsigned)(i2 + o2) < (unsigned)m2;
+            T mz = 1;
+            if (REG && D == 3) mz = mt2[i2 * W2 + o2 + P2];
+#pragma unroll
+            for (int o1 = -P1; o1 <= P1; ++o1) {
+                const bool v1 = v2 && (unsigned)(i1 + o1) < (unsigned)m1;
+                const int xb = i + m0 * (o1 + m1 * o2);
+                T my = 1;
+                if (REG) my = mt1[i1 * W1 + o1 + P1] * mz;
+#pragma unroll
+                for (int o0 = -P0; o0 <= P0; ++o0) {
+                    const bool vv = v1 && (unsigned)(i0 + o0) < (unsigned)m0;
+                    const int o = (o0 + P0) + W0 * ((o1 + P1) + W1 * (o2 + P2));
+                    T a = v[(long long)o * n + s];
+                    if (REG) a += alpha * mt0[i0 * W0 + o0 + P0] * my;
+                    acc += a * x[vv ? xb + o0 : i];
+                }
+            }
+        }
+        if (diag) {
+            constexpr int oc = P0 + W0 * (P1 + W1 * P2);
+            T dd = v[(long long)oc * n + s];
+            if (REG) {
+                T mm = mt0[i0 * W0 + P0] * mt1[i1 * W1 + P1];
+                if (D == 3) mm *= mt2[i2 * W2 + P2];
+                dd += alpha * mm;
+            }
+            *diag = dd;
+        }
+        return acc;
+    }
+
+    template <bool REG>
+    __device__ void sweep_t(int l, bool forward) const {
+        const LevelDesc& L = P->lev[l];
+        const int m0 = L.m[0], m1 = L.m[1], m2 = L.m[2], n = L.n;
+        const T* v = vals(l);
+        T* x = X(l);
+        const T* b = B(l);
+        const T* mt0 = tab + L.mw[0];
+        const T* mt1 = tab + L.mw[1];
+        const T* mt2 = D == 3 ? tab + L.mw[2] : nullptr;
+        const int pp[3] = {P0, P1, P2};
+        for (int cc = 0; cc < NC; ++cc) {
+            const int c = forward ? cc : NC - 1 - cc;
+            const int c0 = c % C0, c1 = (c / C0) % C1, c2 = c / (C0 * C1);
+            const int k0 = ieti_cnt(m0, P0, c0), k1 = ieti_cnt(m1, P1, c1);
+            const int k2 = ieti_cnt(m2, P2, c2);
+            const int off = ieti_color_off(L.m, pp, c0, c1, c2);
+            const int cnt = k0 * k1 * k2;
+            for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+                const int t0 = t % k0, tr = t / k0;
+                const int t1 = tr % k1, t2 = tr / k1;
+                const int i0 = c0 + C0 * t0, i1 = c1 + C1 * t1, i2 = c2 + C2 * t2;
+                if (ieti_masked(mask, L.m, i0, i1, i2)) continue;
+                T d;
+                const T ax = row<REG>(v, n, off + t, x, m0, m1, m2, i0, i1, i2, mt0, mt1, mt2, &d);
+                const int i = i0 + m0 * (i1 + m1 * i2);
+                x[i] += (b[i] - ax) / d;
+            }
+            __syncthreads();
+        }
+    }
+
+    template <bool REG>
+    __device__ void residual_t(int l) const {
+        const LevelDesc& L = P->lev[l];
+        const int m0 = L.m[0], m1 = L.m[1], m2 = L.m[2], n = L.n;
+        const T* v = vals(l);
+        const T* x = X(l);
+        const T* b = B(l);
+        T* r = R(l);
+        const T* mt0 = tab + L.mw[0];
+        const T* mt1 = tab + L.mw[1];
+        const T* mt2 = D == 3 ? tab + L.mw[2] : nullptr;
+        const int pp[3] = {P0, P1, P2};
+        for (int c = 0; c < NC; ++c) {
+            const int c0 = c % C0, c1 = (c / C0) % C1, c2 = c / (C0 * C1);
+            const int k0 = ieti_cnt(m0, P0, c0), k1 = ieti_cnt(m1, P1, c1);
+            const int k2 = ieti_cnt(m2, P2, c2);
+            const int off = ieti_color_off(L.m, pp, c0, c1, c2);
+            const int cnt = k0 * k1 * k2;
+            for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+                const int t0 = t % k0, tr = t / k0;
+                const int t1 = tr % k1, t2 = tr / k1;
+                const int i0 = c0 + C0 * t0, i1 = c1 + C1 * t1, i2 = c2 + C2 * t2;
+                const int i = i0 + m0 * (i1 + m1 * i2);
+                if (ieti_masked(mask, L.m, i0, i1, i2)) {
+                    r[i] = 0;
+                    continue;
+                }
+                r[i] = b[i] - row<REG>(v, n, off + t, x, m0, m1, m2, i0, i1, i2, mt0, mt1, mt2, (T*)nullptr);
+            }
+        }
+        __syncthreads();
+    }
+
+    __device__ void sweep(int l, bool fw) const {
+        if (alpha != T(0)) sweep_t<true>(l, fw);
+        else sweep_t<false>(l, fw);
+    }
+    __device__ void residual(int l) const {
+        if (alpha != T(0)) residual_t<true>(l);
+        else residual_t<false>(l);
+    }
+
+    __device__ void restrict_to(int l) const {
+        const LevelDesc& F = P->lev[l];
+        const LevelDesc& Cl = P->lev[l - 1];
+        const T* r = R(l);
+        T* bc = B(l - 1);
+        T* xc = X(l - 1);
+        for (int I = threadIdx.x; I < Cl.n; I += blockDim.x) {
+            const int I0 = I % Cl.m[0], Ir = I / Cl.m[0];
+            const int I1 = Ir % Cl.m[1], I2 = Ir / Cl.m[1];
+            xc[I] = 0;
+            if (ieti_masked(mask, Cl.m, I0, I1, I2)) {
+                bc[I] = 0;
+                continue;
+            }
+            const int a0 = itab[F.rs[0] + I0], a1 = itab[F.rs[1] + I1];
+            const int a2 = D == 3 ? itab[F.rs[2] + I2] : 0;
+            const T* w0 = tab + F.rw[0] + I0 * R0;
+            const T* w1 = tab + F.rw[1] + I1 * R1;
+            const T* w2 = D == 3 ? tab + F.rw[2] + I2 * R2 : nullptr;
+            T acc = 0;
+#pragma unroll
+            for (int u2 = 0; u2 < R2; ++u2) {
+                const int f2 = a2 + u2;
+                const T ww2 = D == 3 ? w2[u2] : T(1);
+                const bool ok2 = f2 < F.m[2];
+#pragma unroll
+                for (int u1 = 0; u1 < R1; ++u1) {
+                    const int f1 = a1 + u1;
+                    const bool ok1 = ok2 && f1 < F.m[1];
+                    const T ww1 = w1[u1] * ww2;
+                    const T* rr = r + F.m[0] * ((ok1 ? f1 : 0) + F.m[1] * (ok1 ? f2 : 0));
+                    T s = 0;
+#pragma unroll
+                    for (int u0 = 0; u0 < R0; ++u0) {
+                        const int f0 = a0 + u0;
+                        const bool ok = ok1 && f0 < F.m[0];
+                        s += w0[u0] * (ok ? rr[f0] : T(0));
+                    }
+                    acc += ww1 * s;
+                }
+            }
+            bc[I] = acc;
+        }
+        __syncthreads();
+    }
+
+    __device__ void prolong_add(int l) const {
+        const LevelDesc& F = P->lev[l];
+        const LevelDesc& Cl = P->lev[l - 1];
+        const T* xc = X(l - 1);
+        T* x = X(l);
+        for (int i = threadIdx.x; i < F.n; i += blockDim.x) {
+            const int i0 = i % F.m[0], ir = i / F.m[0];
+            const int i1 = ir % F.m[1], i2 = ir / F.m[1];
+            if (ieti_masked(mask, F.m, i0, i1, i2)) continue;
+            const int a0 = itab[F.ps[0] + i0], a1 = itab[F.ps[1] + i1];
+            const int a2 = D == 3 ? itab[F.ps[2] + i2] : 0;
+            const T* w0 = tab + F.pw[0] + i0 * R0;
+            const T* w1 = tab + F.pw[1] + i1 * R1;
+            const T* w2 = D == 3 ? tab + F.pw[2] + i2 * R2 : nullptr;
+            T acc = 0;
+#pragma unroll
+            for (int u2 = 0; u2 < R2; ++u2) {
+                const int c2 = a2 + u2;
+                const T ww2 = D == 3 ? w2[u2] : T(1);
+                const bool ok2 = c2 < Cl.m[2];
+#pragma unroll
+                for (int u1 = 0; u1 < R1; ++u1) {
+                    const int c1 = a1 + u1;
+                    const bool ok1 = ok2 && c1 < Cl.m[1];
+                    const T ww1 = w1[u1] * ww2;
+                    const T* xx = xc + Cl.m[0] * ((ok1 ? c1 : 0) + Cl.m[1] * (ok1 ? c2 : 0));
+                    T s = 0;
+#pragma unroll
+                    for (int u0 = 0; u0 < R0; ++u0) {
+                        const int cc0 = a0 + u0;
+                        const bool ok = ok1 && cc0 < Cl.m[0];
+                        s += w0[u0] * (ok ? xx[cc0] : T(0));
+                    }
+                    acc += ww1 * s;
+                }
+            }
+            x[i] += acc;
+        }
+        __syncthreads();
+    }
+
+    __device__ void coarsest() const {
+        const int n = P->lev[0].n;
+        const T* b = B(0);
+        T* x = X(0);
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            T acc0 = 0, acc1 = 0;
+            int j = 0;
+            for (; j + 1 < n; j += 2) {
+                acc0 += A0[(long long)j * n + i] * b[j];
+                acc1 += A0[(long long)(j + 1) * n + i] * b[j + 1];
+            }
+            if (j < n) acc0 += A0[(long long)j * n + i] * b[j];
+            x[i] = acc0 + acc1;
+        }
+        __syncthreads();
+    }
+
+    __device__ __noinline__ void run(int nu1, int nu2) const {
+        const int L = P->L;
+        if (L == 1) {
+            coarsest();
+            return;
+        }
+        {
+            T* x = X(L - 1);
+            for (int i = threadIdx.x; i < P->lev[L - 1].n; i += blockDim.x) x[i] = 0;
+            __syncthreads();
+        }
+        for (int l = L - 1; l >= 1; --l) {
+            for (int s = 0; s < nu1; ++s) sweep(l, true);
+            residual(l);
+            restrict_to(l);
+        }
+        coarsest();
+        for (int l = 1; l <= L - 1; ++l) {
+            prolong_add(l);
+            for (int s = 0; s < nu2; ++s) sweep(l, false);
+        }
+    }
+};
+
+// FP64 fine-level SpMV row (rows of masked functions return 0)
+template <int D, int P0, int P1, int P2>
+__device__ __forceinline__ double k64_row(const PatchDesc& P, const double* __restrict__ K64, const double* x,
+                                          int i, int mask) {
+    constexpr int W0 = 2 * P0 + 1, W1 = 2 * P1 + 1;
+    const LevelDesc& L = P.lev[P.L - 1];
+    const int m0 = L.m[0], m1 = L.m[1], m2 = L.m[2];
+    const int i0 = i % m0, ir = i / m0;
+    const int i1 = ir % m1, i2 = ir / m1;
+    if (ieti_masked(mask, L.m, i0, i1, i2)) return 0.0;
+    const int pp[3] = {P0, P1, P2};
+    const int s = ieti_store_pos(L.m, pp, i0, i1, i2);
+    const double* v = K64 + L.koff;
+    const int n = L.n;
+    double acc = 0.0;
+#pragma unroll
+    for (int o2 = -P2; o2 <= P2; ++o2) {
+        const bool v2 = (unsigned)(i2 + o2) < (unsigned)m2;
+#pragma unroll
+        for (int o1 = -P1; o1 <= P1; ++o1) {
+            const bool v1 = v2 && (unsigned)(i1 + o1) < (unsigned)m1;
+            const int xb = i + m0 * (o1 + m1 * o2);
+#pragma unroll
+            for (int o0 = -P0; o0 <= P0; ++o0) {
+                const bool vv = v1 && (unsigned)(i0 + o0) < (unsigned)m0;
+                const int o = (o0 + P0) + W0 * ((o1 + P1) + W1 * (o2 + P2));
+                acc += __ldg(v + (long long)o * n + s) * x[vv ? xb + o0 : i];
+            }
+        }
+    }
+    return acc;
+}
+
+// y = K x over the fine level, rows masked by `rowmask` set to 0, and, when
+// `sub` is given, y = sub - K x instead; rows listed by `only` (0 = all rows,
+// 1 = interface rows: boundary rows not on the Dirichlet boundary) or 0.
+template <int D, int P0, int P1, int P2>
+__device__ __noinline__ void spmv64(const PatchDesc& P, const double* __restrict__ K64, const double* x, double* y,
+                                    int rowmask, const double* sub, double scale, int only) {
+    const LevelDesc& F = P.lev[P.L - 1];
+    for (int i = threadIdx.x; i < F.n; i += blockDim.x) {
+        double v = 0.0;
+        bool take = true;
+        if (only == 1) {
+            const int i0 = i % F.m[0], ir = i / F.m[0];
+            const int i1 = ir % F.m[1], i2 = ir / F.m[1];
+            take = ieti_on_boundary(F.m, D, i0, i1, i2) && !ieti_masked(P.dmask, F.m, i0, i1, i2);
+        }
+        if (take) v = scale * k64_row<D, P0, P1, P2>(P, K64, x, i, rowmask);
+        if (sub) v = sub[i] + v;
+        y[i] = v;
+    }
+    __syncthreads();
+}
+
+template <typename T, int D, int P0, int P1, int P2>
+__device__ void vcycle_apply(const VC<T, D, P0, P1, P2>& vc, const double* rin, double* zout, int nu1, int nu2) {
+    const int L = vc.P->L;
+    const int n = vc.P->lev[L - 1].n;
+    T* b = vc.B(L - 1);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) b[i] = (T)rin[i];
+    __syncthreads();
+    vc.run(nu1, nu2);
+    const T* x = vc.X(L - 1);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) zout[i] = (double)x[i];
+    __syncthreads();
+}
+
+__device__ inline void project_kerC(const SolveArgs& a, const PatchDesc& P, double* v, double* coef) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int j = w; j < P.npi; j += nw) {
+        const int row = P.crow0 + j;
+        double d = 0.0, nn = 0.0;
+        for (int e = a.crow_ptr[row] + lane; e < a.crow_ptr[row + 1]; e += 32) {
+            const double ww = a.c_w[e];
+            d += ww * v[a.c_idx[e]];
+            nn += ww * ww;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            d += __shfl_xor_sync(0xffffffffu, d, o);
+            nn += __shfl_xor_sync(0xffffffffu, nn, o);
+        }
+        if (lane == 0) coef[j] = d / nn;
+    }
+    __syncthreads();
+    for (int j = w; j < P.npi; j += nw) {
+        const int row = P.crow0 + j;
+        const double cj = coef[j];
+        for (int e = a.crow_ptr[row] + lane; e < a.crow_ptr[row + 1]; e += 32) v[a.c_idx[e]] -= a.c_w[e] * cj;
+    }
+    __syncthreads();
+}
+
+__device__ inline void apply_C(const SolveArgs& a, const PatchDesc& P, const double* v, double* coef) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int j = w; j < P.npi; j += nw) {
+        const int row = P.crow0 + j;
+        double d = 0.0;
+        for (int e = a.crow_ptr[row] + lane; e < a.crow_ptr[row + 1]; e += 32) d += a.c_w[e] * v[a.c_idx[e]];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+        if (lane == 0) coef[j] = d;
+    }
+    __syncthreads();
+}
+
+template <typename T, int D, int P0, int P1, int P2>
+__global__ void __launch_bounds__(512) k_solve_t(SolveArgs a) {
+    __shared__ Red red;
+    __shared__ double coef[kMaxRows];
+    __shared__ PatchDesc sP;
+    extern __shared__ __align__(16) unsigned char dyn[];
+    const SlotDesc sd = a.slots[blockIdx.x];
+    {
+        const int* src = (const int*)(a.pd + sd.patch);
+        int* dst = (int*)&sP;
+        for (int t = threadIdx.x; t < (int)(sizeof(PatchDesc) / sizeof(int)); t += blockDim.x) dst[t] = src[t];
+    }
+    __syncthreads();
+    const PatchDesc& P = sP;
+    const LevelDesc& F = P.lev[P.L - 1];
+    const int n = F.n;
+    double* x = a.cg + sd.cg;
+    double* r = x + n;
+    double* z = r + n;
+    double* p = z + n;
+    double* q = p + n;
+    const int allsides = D == 2 ? 0xF : 0x3F;
+    const int kind = (a.mode == MODE_SCHUR) ? 1 : 0;
+    const T* Kg = a.mixed ? (const T*)(const void*)a.K32 : (const T*)(const void*)a.K64;
+    const T* A0g = (a.mixed ? (const T*)(const void*)a.A0inv32 : (const T*)(const void*)a.A0inv64) + P.a0off[kind];
+
+    const Plan pl = make_plan(P, sizeof(T), a.smem_bytes);
+    VC<T, D, P0, P1, P2> vc;
+    vc.P = &P;
+    vc.mask = kind == 0 ? P.dmask : allsides;
+    vc.alpha = (kind == 0 && P.floating) ? (T)a.alpha : T(0);
+    vc.Kg = Kg;
+    vc.tab = a.mixed ? (const T*)(const void*)a.tabf : (const T*)(const void*)a.tab;
+    vc.itab = a.itab;
+    vc.nlvec = P.nlvec;
+    vc.lvec = pl.vec ? (T*)dyn : (T*)a.lv + sd.lv;
+    vc.kbase = P.lev[0].koff;
+    vc.ls = pl.ls;
+    vc.Ks = (const T*)(dyn + pl.mat_off);
+    vc.A0 = pl.a0 ? (const T*)(dyn + pl.a0_off) : A0g;
+    // stage the coarsest inverse and coarse-level matrices
+    if (pl.a0) {
+        T* dst = (T*)(dyn + pl.a0_off);
+        const int nn = P.lev[0].n * P.lev[0].n;
+        for (int t = threadIdx.x; t < nn; t += blockDim.x) dst[t] = A0g[t];
+    }
+    if (pl.ls >= 0) {
+        T* dst = (T*)(dyn + pl.mat_off);
+        const long long cnt = P.lev[pl.ls].koff + (long long)P.lev[pl.ls].n * P.lev[pl.ls].S - vc.kbase;
+        const T* src = Kg + vc.kbase;
+        for (long long t = threadIdx.x; t < cnt; t += blockDim.x) dst[t] = src[t];
+    }
+    __syncthreads();
+    long long vcount = 0;
+
+    if (a.mode == MODE_SCHUR) {
+        const double* v = a.in + P.toff;
+        spmv64<D, P0, P1, P2>(P, a.K64, v, r, allsides, nullptr, -1.0, 0);
+        for (int c = 0; c < a.ncycles; ++c) {
+            if (c == 0) {
+                vcycle_apply(vc, r, x, a.nu1, a.nu2);
+            } else {
+                spmv64<D, P0, P1, P2>(P, a.K64, x, q, allsides, r, -1.0, 0);
+                vcycle_apply(vc, q, z, a.nu1, a.nu2);
+                for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] += z[i];
+                __syncthreads();
+            }
+            ++vcount;
+        }
+        for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = v[i] + x[i];
+        __syncthreads();
+        spmv64<D, P0, P1, P2>(P, a.K64, p, a.out + P.toff, 0, nullptr, 1.0, 1);
+        if (threadIdx.x == 0 && a.vstats) {
+            atomicAdd((unsigned long long*)&a.vstats[0], (unsigned long long)vcount);
+            atomicAdd((unsigned long long*)&a.vstats[1], (unsigned long long)(vcount * n));
+        }
+        return;
+    }
+
+    if (a.mode == MODE_VCYCLE) {
+        const double* bb = a.in + P.toff;
+        double* xx = a.out + P.toff;
+        for (int c = 0; c < a.ncycles; ++c) {
+            spmv64<D, P0, P1, P2>(P, a.K64, xx, r, P.dmask, bb, -1.0, 0);
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                const int i0 = i % F.m[0], ir = i / F.m[0];
+                const int i1 = ir % F.m[1], i2 = ir / F.m[1];
+                if (ieti_masked(P.dmask, F.m, i0, i1, i2)) r[i] = 0.0;
+            }
+            __syncthreads();
+            vcycle_apply(vc, r, z, a.nu1, a.nu2);
+            for (int i = threadIdx.x; i < n; i += blockDim.x) xx[i] += z[i];
+            __syncthreads();
+            ++vcount;
+        }
+        if (threadIdx.x == 0 && a.vstats) {
+            atomicAdd((unsigned long long*)&a.vstats[0], (unsigned long long)vcount);
+            atomicAdd((unsigned long long*)&a.vstats[1], (unsigned long long)(vcount * n));
+        }
+        return;
+    }
+
+    const bool basis = a.mode == MODE_BASIS;
+    double* phicol = nullptr;
+    if (basis) {
+        const int lr = sd.row - P.crow0;
+        phicol = a.phi + P.phioff + (long long)lr * n;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            z[i] = 0.0;
+            x[i] = 0.0;
+        }
+        __syncthreads();
+        for (int e = a.crow_ptr[sd.row] + threadIdx.x; e < a.crow_ptr[sd.row + 1]; e += blockDim.x) z[a.c_idx[e]] = 1.0;
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += blockDim.x) phicol[i] = z[i];
+        spmv64<D, P0, P1, P2>(P, a.K64, z, r, P.dmask, nullptr, -1.0, 0);
+        project_kerC(a, P, r, coef);
+    } else {
+        const double* g = a.in + P.toff;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const int i0 = i % F.m[0], ir = i / F.m[0];
+            const int i1 = ir % F.m[1], i2 = ir / F.m[1];
+            r[i] = ieti_masked(P.dmask, F.m, i0, i1, i2) ? 0.0 : g[i];
+            x[i] = 0.0;
+        }
+        __syncthreads();
+        // b = P^T g = g - C^T (Phi^T g)
+        {
+            const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+            for (int j = w; j < P.npi; j += nw) {
+                const int row = P.crow0 + j;
+                const double cj = a.rpi_loc[row];
+                for (int e = a.crow_ptr[row] + lane; e < a.crow_ptr[row + 1]; e += 32) r[a.c_idx[e]] -= a.c_w[e] * cj;
+            }
+        }
+        __syncthreads();
+        if (P.floating) {
+            double s[1] = {0.0};
+            for (int i = threadIdx.x; i < n; i += blockDim.x) s[0] += r[i];
+            cta_sum<1>(s, red);
+            const double mean = s[0] / n;
+            for (int i = threadIdx.x; i < n; i += blockDim.x) r[i] -= mean;
+            __syncthreads();
+        }
+    }
+    double nb2;
+    {
+        double s[1] = {0.0};
+        for (int i = threadIdx.x; i < n; i += blockDim.x) s[0] += r[i] * r[i];
+        cta_sum<1>(s, red);
+        nb2 = s[0];
+    }
+    int it = 0;
+    bool conv = nb2 == 0.0;
+    const double tol2 = a.tol * a.tol * nb2;
+    if (!conv) {
+        vcycle_apply(vc, r, z, a.nu1, a.nu2);
+        ++vcount;
+        if (basis) project_kerC(a, P, z, coef);
+        double rz;
+        {
+            double s[1] = {0.0};
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                p[i] = z[i];
+                s[0] += r[i] * z[i];
+            }
+            cta_sum<1>(s, red);
+            rz = s[0];
+        }
+        for (it = 1; it <= a.maxit; ++it) {
+            double s[1] = {0.0};
+            spmv64<D, P0, P1, P2>(P, a.K64, p, q, P.dmask, nullptr, 1.0, 0);
+            if (basis) project_kerC(a, P, q, coef);
+            for (int i = threadIdx.x; i < n; i += blockDim.x) s[0] += p[i] * q[i];
+            cta_sum<1>(s, red);
+            const double pq = s[0];
+            if (!(pq > 0.0) || !isfinite(pq)) {
+                if (threadIdx.x == 0) atomicOr(a.flags, IETI_FLAG_BREAKDOWN);
+                break;
+            }
+            const double alpha = rz / pq;
+            double s2[1] = {0.0};
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                x[i] += alpha * p[i];
+                const double ri = r[i] - alpha * q[i];
+                r[i] = ri;
+                s2[0] += ri * ri;
+            }
+            cta_sum<1>(s2, red);
+            if (s2[0] <= tol2) {
+                conv = true;
+                break;
+            }
+            vcycle_apply(vc, r, z, a.nu1, a.nu2);
+            ++vcount;
+            if (basis) project_kerC(a, P, z, coef);
+            double s3[2] = {0.0, 0.0};
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                s3[0] += r[i] * z[i];
+                s3[1] += q[i] * z[i];
+            }
+            cta_sum<2>(s3, red);
+            const double beta = a.mixed ? -alpha * s3[1] / rz : s3[0] / rz;
+            rz = s3[0];
+            for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = z[i] + beta * p[i];
+            __syncthreads();
+        }
+        if (!conv && it > a.maxit) it = a.maxit;
+    }
+    if (threadIdx.x == 0) {
+        a.its[blockIdx.x] = it;
+        if (!conv) atomicOr(a.flags, IETI_FLAG_NOT_CONVERGED);
+        if (a.vstats) {
+            atomicAdd((unsigned long long*)&a.vstats[0], (unsigned long long)vcount);
+            atomicAdd((unsigned long long*)&a.vstats[1], (unsigned long long)(vcount * n));
+            atomicAdd((unsigned long long*)&a.vstats[2], (unsigned long long)it);
+            atomicMax((unsigned long long*)&a.vstats[3], (unsigned long long)it);
+            if (nb2 > 0.0) atomicAdd((unsigned long long*)&a.vstats[4], 1ULL);
+        }
+    }
+    if (basis) {
+        for (int i = threadIdx.x; i < n; i += blockDim.x) phicol[i] += x[i];
+        return;
+    }
+    apply_C(a, P, x, coef);
+    for (int j = threadIdx.x; j < P.npi; j += blockDim.x) coef[j] -= a.upi_loc[P.crow0 + j];
+    __syncthreads();
+    double* out = a.out + P.toff;
+    const double* ph = a.phi + P.phioff;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double u = x[i];
+        for (int j = 0; j < P.npi; ++j) u -= coef[j] * ph[(long long)j * n + i];
+        out[i] = u;
+    }
+}
+
+template <typename T, int D, int P0, int P1, int P2>
+cudaError_t launch_t(const SolveArgs& a, int threads, cudaStream_t st) {
+    if (a.nslots == 0) return cudaSuccess;
+    auto kern = k_solve_t<T, D, P0, P1, P2>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)a.smem_bytes);
+    if (e != cudaSuccess) return e;
+    kern<<<a.nslots, threads, a.smem_bytes, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace ieti_t
