@@ -208,6 +208,23 @@ int ietidp_solve_host(ietidp_handle* h, const double* f_host, double* u_host,
  * device vectors in patch layout.  Used to measure V-cycle throughput. */
 int ietidp_vcycles(ietidp_handle* h, const double* b, double* x, int ncycles);
 
+/* Same V-cycles as ietidp_vcycles, but allocating nothing: for callers that
+ * cannot allocate device memory when they run (a plugin inside a host
+ * framework that owns the device memory pool, a latency-bound loop that must
+ * not call cudaMalloc/cudaFree).  The paper has no counterpart; this is a
+ * deployment variant of the V-cycle kernel.  The kernel's scratch vectors
+ * (FP64 residual and correction, per-level vectors of every patch) live in
+ * one static device array of 16 MiB per device, held by every device that
+ * loads the library until the process exits.  The handle's device must be
+ * current; the first call on a device looks up the array's address (with
+ * that device current).  Problems whose scratch exceeds 16 MiB are rejected
+ * with IETIDP_E_INVALID_ARG and a message giving both sizes.  All calls on a
+ * device share the array and it keeps the last call's contents (the kernel
+ * writes every scratch entry before reading it, so nothing needs clearing);
+ * calls whose work overlaps on the GPU (other streams, other handles, other
+ * host threads) race on it.  b, x as for ietidp_vcycles. */
+int ietidp_vcycles_noalloc(ietidp_handle* h, const double* b, double* x, int ncycles);
+
 /* Helpers exposed for testing the building blocks against the oracle:
  *  - ietidp_apply_K: y = K x per patch (Dirichlet rows/cols removed);
  *  - ietidp_apply_F: q = F p on the multipliers (device, n_lambda);

@@ -13,6 +13,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <tuple>
@@ -172,6 +173,9 @@ struct ietidp_handle {
     double basis_it_avg = 0;
     int basis_it_max = 0;
     int n_floating = 0;
+    int device = 0;                 // device current at setup
+    long long cg_patch_elems = 0;   // FP64 scratch used by the per-patch slots
+    long long lv_patch_elems = 0;   // level-vector scratch used by the per-patch slots
 };
 
 extern "C" const char* ietidp_last_error(void) { return g_err.c_str(); }
@@ -626,6 +630,7 @@ extern "C" int ietidp_setup(const iga_problem* P, const ietidp_options* opt_in, 
     int d = P->dim, N = P->npatch;
     h->npatch = N;
     h->dim = d;
+    CUH(cudaGetDevice(&h->device));
     // ---- primal objects and constraint rows -------------------------------
     // object kind of a class: number of directions in which its first copy
     // lies on the patch boundary
@@ -979,6 +984,8 @@ extern "C" int ietidp_setup(const iga_problem* P, const ietidp_options* opt_in, 
             lv_total += 3 * nl;
         }
         for (int k = 0; k < N; ++k) sp[k] = SlotDesc{k, 0, 0, 0, cgo[k], lvo[k]};
+        h->cg_patch_elems = N < nslots_max ? cgo[N] : cg_total;
+        h->lv_patch_elems = N < nslots_max ? lvo[N] : lv_total;
         for (int s = 0; s < nslot_basis; ++s) sb[s] = SlotDesc{crow_patch[s], 0, s, 0, cgo[s], lvo[s]};
     }
     CKH(h->mem.alloc(&h->cg, cg_total));
@@ -1371,4 +1378,64 @@ extern "C" int ietidp_destroy(ietidp_handle* h) {
     if (h->fork) cudaEventDestroy(h->fork);
     delete h;
     return IETIDP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// V-cycles without any device allocation.
+//
+// Some callers cannot allocate device memory at the point where they want to
+// run the smoother: a plugin running inside a host framework that owns the
+// device memory pool and forbids allocations outside it, or a latency-bound
+// loop that must not hit cudaMalloc/cudaFree (they may synchronize the device
+// and take unbounded time).  For them the scratch vectors of the V-cycle
+// kernel (the FP64 residual/correction vectors and the per-level vectors of
+// every patch) live in one file-scope device array of fixed size instead of
+// the handle's own buffers.  Its device address is looked up once per device
+// with that device current (the first call on a device does it); every call
+// on that device then shares the same array.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr size_t kNoAllocScratchBytes = 16u << 20;   // 16 MiB per device, held until exit
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kNoAllocMaxDevices] = {};
+}  // namespace
+
+extern "C" int ietidp_vcycles_noalloc(ietidp_handle* h, const double* b, double* x, int ncycles) {
+    if (!h || !b || !x || ncycles < 0) return fail(IETIDP_E_INVALID_ARG, "bad argument");
+    int dev = -1;
+    CU(cudaGetDevice(&dev));
+    if (dev != h->device) return fail(IETIDP_E_INVALID_ARG, "the handle's device must be the current device");
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(IETIDP_E_INVALID_ARG, "device ordinal out of range");
+    const size_t tsz = h->opt.precision == IETIDP_PREC_MIXED ? sizeof(float) : sizeof(double);
+    const size_t cg_bytes = ((size_t)h->cg_patch_elems * sizeof(double) + 255) & ~(size_t)255;
+    const size_t need = cg_bytes + (size_t)h->lv_patch_elems * tsz;
+    if (need > kNoAllocScratchBytes)
+        return fail(IETIDP_E_INVALID_ARG, "problem needs " + std::to_string(need) +
+                                              " bytes of V-cycle scratch; the static limit is " +
+                                              std::to_string(kNoAllocScratchBytes) + " bytes");
+    void* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_addr[dev]) {
+            void* p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess) return fail(IETIDP_E_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+            g_noalloc_addr[dev] = p;
+        }
+        base = g_noalloc_addr[dev];
+    }
+    // run the same V-cycle launch with the scratch pointers redirected
+    double* save_cg = h->cg;
+    void* save_lv = h->lv;
+    ietidp_options save = h->opt;
+    h->cg = (double*)base;
+    h->lv = (unsigned char*)base + cg_bytes;
+    h->opt.dirichlet_vcycles = ncycles;
+    int rc = run_solve(h, MODE_VCYCLE, h->gpatch, b, x, 0.0, 0, h->vst);
+    h->opt = save;
+    h->cg = save_cg;
+    h->lv = save_lv;
+    return rc;
 }

@@ -92,6 +92,7 @@ _SIGS = {
     "ietidp_solve": (C.c_int, [_vp, _vp, _vp, C.POINTER(ietidp_stats)]),
     "ietidp_solve_host": (C.c_int, [_vp, _vp, _vp, C.POINTER(ietidp_stats)]),
     "ietidp_vcycles": (C.c_int, [_vp, _vp, _vp, C.c_int]),
+    "ietidp_vcycles_noalloc": (C.c_int, [_vp, _vp, _vp, C.c_int]),
     "ietidp_apply_K": (C.c_int, [_vp, _vp, _vp]),
     "ietidp_apply_F": (C.c_int, [_vp, _vp, _vp]),
     "ietidp_apply_precond": (C.c_int, [_vp, _vp, _vp]),
@@ -288,6 +289,11 @@ class Solver:
 
     def vcycles(self, b, x, ncycles):
         _check(_lib.ietidp_vcycles(self.h, _ptr(b), _ptr(x), int(ncycles)))
+
+    def vcycles_noalloc(self, b, x, ncycles):
+        """V-cycles whose scratch is the library's static device array (no
+        allocation; see ietidp_vcycles_noalloc in the header)."""
+        _check(_lib.ietidp_vcycles_noalloc(self.h, _ptr(b), _ptr(x), int(ncycles)))
 
     def apply_K(self, x, y):
         _check(_lib.ietidp_apply_K(self.h, _ptr(x), _ptr(y)))
