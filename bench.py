@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--vcycle-reps", type=int, default=50)
+    ap.add_argument("--mode", default="bench", choices=["bench", "vcycle"],
+                    help="vcycle: setup plus three batched V-cycle launches (profiling target)")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     return ap.parse_args()
 
 
@@ -237,10 +240,32 @@ def time_path(api, torch, prob, prec, args, flush, stream):
     return sol, u, ms, stats, setup_ms
 
 
+def run_vcycle_probe(args):
+    """Setup of the workload and three batched V-cycle launches over the
+    Neumann hierarchies of all patches (a short, self-contained profiling
+    target for the dominant kernel)."""
+    import torch
+    from paper_1705_04531_gb300 import build
+    build.build()
+    from paper_1705_04531_gb300 import ietidp as api
+    dom = workload(args.workload)
+    prob = api.Problem(dom)
+    sol = api.Solver(prob, precision=args.precision)
+    f = prob.load()
+    x = torch.zeros_like(f)
+    for _ in range(3):
+        sol.vcycles(f, x, 1)
+    torch.cuda.synchronize()
+    print(json.dumps({"mode": "vcycle", "workload": args.workload, "precision": args.precision,
+                      "x_norm": float(x.norm())}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "vcycle":
+        return run_vcycle_probe(args)
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -15,8 +15,7 @@ SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libietidp.so")
 SOURCES = ["setup_kernels.cu", "solver_kernels.cu", "dual_kernels.cu", "ietidp_host.cu",
-           "solver_dispatch.cu", "solver_t_3d.cu"] + [
-    f"solver_t_{t}_2d_p{p}.cu" for t in ("f32", "f64") for p in (2, 3, 4)]
+           "solver_dispatch.cu"] + sorted(f for f in os.listdir(SRC) if f.startswith("solver_t_"))
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

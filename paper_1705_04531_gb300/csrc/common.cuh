@@ -6,13 +6,15 @@
 // xi_r = 1; a masked side's functions are removed from the operator (their
 // rows are skipped, their vector entries stay 0).
 //
-// Banded stiffness storage ("color-major ELL"): for a level with n functions
-// and stencil size S = prod_r (2 p_r + 1), values[o * n + s] holds
-// K(i, i + offset(o)) where s is the storage position of row i.  Rows are
-// stored color by color (color c = sum_r (i_r mod (p_r+1)) * stride_r, the
-// multicolor Gauss-Seidel classes), and within a color in lexicographic order
-// of t_r = i_r / (p_r+1).  A warp working on one color therefore reads each
-// stencil diagonal with unit stride.
+// Banded stiffness storage: for a level with n functions and stencil size
+// S = prod_r (2 p_r + 1), values[s * Sp + o] holds K(i, i + offset(o)) where s
+// is the storage position of row i and Sp >= S the padded row length (a
+// multiple of 4 with Sp/4 odd, so that 16-byte row loads by consecutive
+// threads fall in distinct shared-memory bank groups).  Rows are stored color
+// by color (color c = sum_r (i_r mod (p_r+1)) * stride_r, the multicolor
+// Gauss-Seidel classes), and within a color in lexicographic order of
+// t_r = i_r / (p_r+1): the rows one color step touches are one contiguous
+// block.  Out-of-grid stencil entries are stored as 0.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -25,6 +27,9 @@ struct LevelDesc {
     int m[3];          // functions per direction (1 for unused directions)
     int n;             // m0*m1*m2
     int S;             // stencil size
+    int Sp;            // padded row length of the value arrays
+    int xoff, boff;    // specialised solver: offsets of x (color-major, ghost padded) and b (storage order)
+    int nx;            // size of the color-major padded x of this level
     int refined[3];    // 1 if this level halves the elements of level l-1 along r
     long long koff;    // offset of this level's values in the value arrays
     int voff;          // offset of this level's vectors in a slot's level block
@@ -48,6 +53,7 @@ struct PatchDesc {
     long long toff;      // offset of this patch in torn vectors
     int n;               // fine functions
     int nlvec;           // sum over levels of n_l
+    int nlx, nlb;        // specialised solver: total x and b sizes over levels
     long long a0off[2];  // coarsest inverse (n0 x n0), hierarchy 0 (Neumann) / 1 (Dirichlet)
     int npi;             // primal constraint rows of this patch
     int crow0;           // first global C row of this patch
@@ -82,6 +88,29 @@ __host__ __device__ inline int ieti_store_pos(const int* m, const int* p, int i0
 }
 
 __host__ __device__ inline int ieti_ncolors(const int* p) { return (p[0] + 1) * (p[1] + 1) * (p[2] + 1); }
+
+// padded row length: multiple of 4 with an odd number of 4-groups
+__host__ __device__ inline int ieti_sp(int S) {
+    int sp = (S + 3) & ~3;
+    if ((sp / 4) % 2 == 0) sp += 4;
+    return sp;
+}
+
+// color-major, ghost-padded vector layout of the specialised solver: color c
+// owns a (k0+2) x (k1+2) [x (k2+2)] block (one ghost layer per side, d = 3
+// only in direction 2); blocks follow each other in color order.
+__host__ __device__ inline int ieti_cm_block(const int* m, const int* p, int dim, int c0, int c1, int c2) {
+    int b = (ieti_cnt(m[0], p[0], c0) + 2) * (ieti_cnt(m[1], p[1], c1) + 2);
+    if (dim == 3) b *= ieti_cnt(m[2], p[2], c2) + 2;
+    return b;
+}
+__host__ __device__ inline int ieti_cm_size(const int* m, const int* p, int dim) {
+    int s = 0;
+    for (int c2 = 0; c2 < (dim == 3 ? p[2] + 1 : 1); ++c2)
+        for (int c1 = 0; c1 < p[1] + 1; ++c1)
+            for (int c0 = 0; c0 < p[0] + 1; ++c0) s += ieti_cm_block(m, p, dim, c0, c1, c2);
+    return s;
+}
 
 __host__ __device__ inline bool ieti_masked(int mask, const int* m, int i0, int i1, int i2) {
     if ((mask & 1) && i0 == 0) return true;

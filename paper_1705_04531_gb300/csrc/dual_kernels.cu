@@ -117,7 +117,7 @@ __device__ __forceinline__ double k64_apply_row(const PatchDesc& P, const double
         for (int o1 = lo1; o1 <= hi1; ++o1) {
             int ob = ((o2 + P.p[2]) * w1 + (o1 + P.p[1])) * w0 + P.p[0];
             int xb = i0 + L.m[0] * ((i1 + o1) + L.m[1] * (i2 + o2));
-            for (int o0 = lo0; o0 <= hi0; ++o0) acc += vals[(long long)(ob + o0) * L.n + s] * x[xb + o0];
+            for (int o0 = lo0; o0 <= hi0; ++o0) acc += vals[(long long)s * L.Sp + ob + o0] * x[xb + o0];
         }
     return acc;
 }

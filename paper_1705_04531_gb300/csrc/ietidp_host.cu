@@ -108,6 +108,7 @@ struct iga_problem {
     DevMem mem;
     double* K64 = nullptr;           // fine stiffness (per patch, color-major)
     std::vector<long long> koff;     // per patch offset in K64
+    std::vector<int> Sp;             // per patch padded row length
     double* f = nullptr;             // load (torn)
 };
 
@@ -131,6 +132,8 @@ struct ietidp_handle {
     PatchDesc* d_pd = nullptr;
     double* K64 = nullptr;
     float* K32 = nullptr;
+    double* KM64 = nullptr;   // K + alpha M^ on floating patches (same offsets as K64)
+    float* KM32 = nullptr;
     double* tab = nullptr;
     float* tabf = nullptr;
     int* itab = nullptr;
@@ -374,10 +377,11 @@ extern "C" int iga_assemble_patches(const iga_domain_desc* D, void* stream, iga_
             L.n *= L.m[r];
             L.S *= 2 * q.p[r] + 1;
         }
+        L.Sp = ieti_sp(L.S);
         q.n = L.n;
         L.koff = koff;
         P->koff[k] = koff;
-        koff += (long long)L.n * L.S;
+        koff += (long long)L.n * L.Sp;
         max_S = std::max(max_S, L.S);
         long long nqp = 1;
         for (int r = 0; r < 3; ++r) {
@@ -504,7 +508,7 @@ static int launch_group(ietidp_handle* h, SolveArgs a, const SlotGroup& g, cudaS
     a.its = h->its + g.its_off;
     a.smem_bytes = g.smem;
     cudaError_t e;
-    if (solve_variant_exists(g.dim, g.p0, g.p1, g.p2)) e = launch_solve_variant(a, g.dim, g.p0, g.p1, g.p2, 512, st);
+    if (solve_variant_exists(g.dim, g.p0, g.p1, g.p2, a.mixed)) e = launch_solve_variant(a, g.dim, g.p0, g.p1, g.p2, 512, st);
     else e = launch_solve(a, 512, st);
     h->launches += 1;
     if (e != cudaSuccess) return fail(IETIDP_E_CUDA, std::string("solve kernel: ") + cudaGetErrorString(e));
@@ -519,6 +523,8 @@ static int run_solve(ietidp_handle* h, int mode, const std::vector<SlotGroup>& g
     a.mixed = h->opt.precision == IETIDP_PREC_MIXED;
     a.K64 = h->K64;
     a.K32 = h->K32;
+    a.KM64 = h->KM64;
+    a.KM32 = h->KM32;
     a.tab = h->tab;
     a.tabf = h->tabf;
     a.itab = h->itab;
@@ -799,7 +805,7 @@ extern "C" int ietidp_setup(const iga_problem* P, const ietidp_options* opt_in, 
         q.floating = q.dmask == 0;
         if (q.floating) h->n_floating++;
         q.toff = P->toff[k];
-        int voff = 0;
+        int voff = 0, xoff = 0, boff = 0;
         for (int l = 0; l < q.L; ++l) {
             LevelDesc& L = q.lev[l];
             L.n = 1;
@@ -810,10 +816,17 @@ extern "C" int ietidp_setup(const iga_problem* P, const ietidp_options* opt_in, 
                 L.S *= 2 * q.p[r] + 1;
                 L.refined[r] = (l > 0 && r < d && sch[l][r] != sch[l - 1][r]) ? 1 : 0;
             }
+            L.Sp = ieti_sp(L.S);
+            koff = (koff + 3) & ~3LL;
             L.koff = koff;
-            koff += (long long)L.n * L.S;
+            koff += (long long)L.n * L.Sp;
             L.voff = voff;
             voff += L.n;
+            L.nx = l >= 1 ? ieti_cm_size(L.m, q.p, d) : L.n;
+            L.xoff = xoff;
+            xoff += (L.nx + 3) & ~3;
+            L.boff = boff;
+            boff += (L.n + 3) & ~3;
             max_S = std::max(max_S, L.S);
             max_rows_lev = std::max(max_rows_lev, L.n);
             for (int r = 0; r < d; ++r) {
@@ -837,6 +850,8 @@ extern "C" int ietidp_setup(const iga_problem* P, const ietidp_options* opt_in, 
         }
         q.n = q.lev[q.L - 1].n;
         q.nlvec = voff;
+        q.nlx = xoff;
+        q.nlb = boff;
         int n0 = q.lev[0].n;
         max_n0 = std::max(max_n0, n0);
         q.a0off[0] = a0off;
@@ -856,6 +871,10 @@ extern "C" int ietidp_setup(const iga_problem* P, const ietidp_options* opt_in, 
     CKH(h->mem.upload(&h->d_pd, h->pd, st));
     CKH(h->mem.alloc(&h->K64, koff));
     if (mixed) CKH(h->mem.alloc(&h->K32, koff));
+    if (h->n_floating > 0) {
+        CKH(h->mem.alloc(&h->KM64, koff));
+        if (mixed) CKH(h->mem.alloc(&h->KM32, koff));
+    }
     CKH(h->mem.alloc(&h->tab, toff_tab));
     CKH(h->mem.alloc(&h->tabf, toff_tab));
     CKH(h->mem.alloc(&h->itab, itoff));
@@ -914,7 +933,7 @@ extern "C" int ietidp_setup(const iga_problem* P, const ietidp_options* opt_in, 
     for (int k = 0; k < N; ++k) {
         const PatchDesc& q = h->pd[k];
         const LevelDesc& F = q.lev[q.L - 1];
-        CUH(cudaMemcpyAsync(h->K64 + F.koff, P->K64 + P->koff[k], sizeof(double) * F.n * F.S,
+        CUH(cudaMemcpyAsync(h->K64 + F.koff, P->K64 + P->koff[k], sizeof(double) * F.n * F.Sp,
                             cudaMemcpyDeviceToDevice, st));
     }
     // ---- multigrid tables, Galerkin hierarchy, coarsest inverses -----------
@@ -947,7 +966,10 @@ extern "C" int ietidp_setup(const iga_problem* P, const ietidp_options* opt_in, 
         if (e == cudaSuccess)
             e = launch_coarse_inverse(h->d_pd, N, h->K64, h->tab, opt.alpha_reg, h->A0inv64, h->A0inv32, work,
                                       max_n0, h->flags, st);
+        if (e == cudaSuccess && h->n_floating > 0)
+            e = launch_regularize(h->d_pd, N, h->K64, h->tab, opt.alpha_reg, h->KM64, st);
         if (e == cudaSuccess && mixed) e = launch_to_f32(h->K64, h->K32, koff, st);
+        if (e == cudaSuccess && mixed && h->n_floating > 0) e = launch_to_f32(h->KM64, h->KM32, koff, st);
         if (e == cudaSuccess) e = launch_to_f32(h->tab, h->tabf, toff_tab, st);
         if (e == cudaSuccess)
             e = launch_cweights(h->d_pd, h->nrows, h->crow_ptr, h->crow_patch, d_tang, h->c_idx, h->c_w, st);
@@ -968,20 +990,24 @@ extern "C" int ietidp_setup(const iga_problem* P, const ietidp_options* opt_in, 
     {
         // slot s serves basis row s (if s < nrows) and patch s (if s < N)
         std::vector<long long> cgo(nslots_max), lvo(nslots_max);
+        auto lvneed = [&](const PatchDesc& q) {
+            return std::max<long long>(3LL * q.nlvec, (long long)q.nlx + q.nlb + q.n + 4);
+        };
         for (int s = 0; s < nslots_max; ++s) {
             long long n = 0, nl = 0;
             if (s < nslot_basis) {
                 n = std::max<long long>(n, h->pd[crow_patch[s]].n);
-                nl = std::max<long long>(nl, h->pd[crow_patch[s]].nlvec);
+                nl = std::max<long long>(nl, lvneed(h->pd[crow_patch[s]]));
             }
             if (s < N) {
                 n = std::max<long long>(n, h->pd[s].n);
-                nl = std::max<long long>(nl, h->pd[s].nlvec);
+                nl = std::max<long long>(nl, lvneed(h->pd[s]));
             }
+            nl = (nl + 3) & ~3LL;
             cgo[s] = cg_total;
             lvo[s] = lv_total;
             cg_total += 5 * n;
-            lv_total += 3 * nl;
+            lv_total += nl;
         }
         for (int k = 0; k < N; ++k) sp[k] = SlotDesc{k, 0, 0, 0, cgo[k], lvo[k]};
         h->cg_patch_elems = N < nslots_max ? cgo[N] : cg_total;

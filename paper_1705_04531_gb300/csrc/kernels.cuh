@@ -50,6 +50,8 @@ cudaError_t launch_coarse_inverse(const PatchDesc* pd, int npatch, const double*
 
 // Constraint weights: entries of C rows (vertex = 1, edge/face = normalized
 // integrals of the tangential basis functions).
+cudaError_t launch_regularize(const PatchDesc* pd, int npatch, const double* K64, const double* tab, double alpha,
+                              double* KM64, cudaStream_t st);
 cudaError_t launch_cweights(const PatchDesc* pd, int nrows, const int* crow_ptr,
                             const int* crow_patch, const int* crow_tang, const int* c_idx,
                             double* c_w, cudaStream_t st);
@@ -80,6 +82,8 @@ struct SolveArgs {
     int mixed;                 // V-cycles in FP32
     const double* K64;
     const float* K32;
+    const double* KM64;        // K + alpha M^ (floating patches), all levels
+    const float* KM32;
     const double* tab;
     const float* tabf;
     const int* itab;
@@ -109,7 +113,7 @@ struct SolveArgs {
 // generic kernel (degrees known at run time only)
 cudaError_t launch_solve(const SolveArgs& a, int threads, cudaStream_t st);
 // kernel specialised for (dim, p0, p1, p2); cudaErrorNotSupported if none exists
-bool solve_variant_exists(int dim, int p0, int p1, int p2);
+bool solve_variant_exists(int dim, int p0, int p1, int p2, int mixed);
 cudaError_t launch_solve_variant(const SolveArgs& a, int dim, int p0, int p1, int p2, int threads,
                                  cudaStream_t st);
 // shared memory a specialised launch would use for this patch (uncapped)

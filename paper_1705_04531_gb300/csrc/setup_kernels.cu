@@ -305,7 +305,7 @@ __global__ void k_stiffness(SetupArgs a, long long total_rows) {
                                     }
                                 }
         }
-        a.K64[F.koff + (long long)o * F.n + s] = acc;
+        a.K64[F.koff + (long long)s * F.Sp + o] = acc;
     }
 }
 
@@ -537,11 +537,11 @@ __global__ void k_galerkin(const PatchDesc* pd, const int* plist, int depth, dou
                                         mul *= 2 * P.p[r] + 1;
                                     }
                                     if (!ok2 || pb == 0.0) continue;
-                                    acc += pa * pb * K64[F.koff + (long long)of * F.n + sa];
+                                    acc += pa * pb * K64[F.koff + (long long)sa * F.Sp + of];
                                 }
                     }
         }
-        K64[C.koff + (long long)O * C.n + s] = acc;
+        K64[C.koff + (long long)s * C.Sp + O] = acc;
     }
 }
 
@@ -620,7 +620,7 @@ __global__ void k_coarse_inverse(const PatchDesc* pd, const double* K64, const d
             }
             if (band) {
                 int s = ieti_store_pos(L.m, P.p, ii[0], ii[1], ii[2]);
-                v = K64[L.koff + (long long)of * n + s] + al * mprod;
+                v = K64[L.koff + (long long)s * L.Sp + of] + al * mprod;
             }
         }
         A[t] = v;
@@ -633,6 +633,51 @@ __global__ void k_coarse_inverse(const PatchDesc* pd, const double* K64, const d
         for (int kk = max(i, j); kk < n; ++kk) s += Li[(long long)kk * n + i] * Li[(long long)kk * n + j];
         A0inv64[P.a0off[kind] + t] = s;
         A0inv32[P.a0off[kind] + t] = (float)s;
+    }
+}
+
+// KM = K + alpha M^ on every level of the floating patches (M^ the Kronecker
+// product of the 1D parameter mass bands of that level); other patches untouched
+__global__ void k_regularize(const PatchDesc* pd, const double* K64, const double* tab, double alpha, double* KM64) {
+    const PatchDesc& P = pd[blockIdx.y];
+    if (!P.floating) return;
+    for (int l = 0; l < P.L; ++l) {
+        const LevelDesc& L = P.lev[l];
+        long long total = (long long)L.n * L.Sp;
+        for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+             t += (long long)gridDim.x * blockDim.x) {
+            int s = (int)(t / L.Sp), o = (int)(t % L.Sp);
+            double v = K64[L.koff + t];
+            if (o < L.S) {
+                // natural row of storage position s
+                int ncol = ieti_ncolors(P.p), c = 0, off = 0;
+                int cc0 = 0, cc1 = 0, cc2 = 0, k0 = 1, k1 = 1;
+                for (c = 0; c < ncol; ++c) {
+                    int c0 = c % (P.p[0] + 1), c1 = (c / (P.p[0] + 1)) % (P.p[1] + 1), c2 = c / ((P.p[0] + 1) * (P.p[1] + 1));
+                    int o2 = ieti_color_off(L.m, P.p, c0, c1, c2);
+                    int cnt = ieti_cnt(L.m[0], P.p[0], c0) * ieti_cnt(L.m[1], P.p[1], c1) * ieti_cnt(L.m[2], P.p[2], c2);
+                    if (s >= o2 && s < o2 + cnt) {
+                        cc0 = c0; cc1 = c1; cc2 = c2; off = o2;
+                        k0 = ieti_cnt(L.m[0], P.p[0], c0);
+                        k1 = ieti_cnt(L.m[1], P.p[1], c1);
+                        break;
+                    }
+                }
+                int tt = s - off;
+                int i0 = cc0 + (P.p[0] + 1) * (tt % k0), i1 = cc1 + (P.p[1] + 1) * ((tt / k0) % k1),
+                    i2 = cc2 + (P.p[2] + 1) * (tt / (k0 * k1));
+                int ii[3] = {i0, i1, i2}, rem = o;
+                double mm = 1.0;
+                for (int r = 0; r < 3; ++r) {
+                    int w = 2 * P.p[r] + 1;
+                    int orr = rem % w;
+                    rem /= w;
+                    if (r < P.dim) mm *= tab[L.mw[r] + ii[r] * w + orr];
+                }
+                v += alpha * mm;
+            }
+            KM64[L.koff + t] = v;
+        }
     }
 }
 
@@ -722,6 +767,12 @@ cudaError_t launch_coarse_inverse(const PatchDesc* pd, int npatch, const double*
                                   double alpha, double* A0inv64, float* A0inv32, double* work, int max_n0,
                                   int* flags, cudaStream_t st) {
     k_coarse_inverse<<<npatch * 2, 256, 0, st>>>(pd, K64, tab, alpha, A0inv64, A0inv32, work, max_n0, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_regularize(const PatchDesc* pd, int npatch, const double* K64, const double* tab, double alpha,
+                              double* KM64, cudaStream_t st) {
+    k_regularize<<<dim3(64, npatch), 256, 0, st>>>(pd, K64, tab, alpha, KM64);
     return cudaGetLastError();
 }
 

@@ -1,5 +1,6 @@
 // Dispatch of the local solver to the kernel specialised for the patch
-// dimension and degrees.
+// dimension and degrees (FP32 V-cycles: 2D degrees 2..4 in each direction
+// and 3D degree 2; FP64 V-cycles: 2D (2,2), (3,3) and 3D degree 2).
 #include "solver_impl.cuh"
 
 namespace ieti_t {
@@ -14,50 +15,50 @@ extern template cudaError_t launch_t<float, 2, 4, 3, 0>(const SolveArgs&, int, c
 extern template cudaError_t launch_t<float, 2, 4, 4, 0>(const SolveArgs&, int, cudaStream_t);
 extern template cudaError_t launch_t<float, 3, 2, 2, 2>(const SolveArgs&, int, cudaStream_t);
 extern template cudaError_t launch_t<double, 2, 2, 2, 0>(const SolveArgs&, int, cudaStream_t);
-extern template cudaError_t launch_t<double, 2, 2, 3, 0>(const SolveArgs&, int, cudaStream_t);
-extern template cudaError_t launch_t<double, 2, 2, 4, 0>(const SolveArgs&, int, cudaStream_t);
-extern template cudaError_t launch_t<double, 2, 3, 2, 0>(const SolveArgs&, int, cudaStream_t);
 extern template cudaError_t launch_t<double, 2, 3, 3, 0>(const SolveArgs&, int, cudaStream_t);
-extern template cudaError_t launch_t<double, 2, 3, 4, 0>(const SolveArgs&, int, cudaStream_t);
-extern template cudaError_t launch_t<double, 2, 4, 2, 0>(const SolveArgs&, int, cudaStream_t);
-extern template cudaError_t launch_t<double, 2, 4, 3, 0>(const SolveArgs&, int, cudaStream_t);
-extern template cudaError_t launch_t<double, 2, 4, 4, 0>(const SolveArgs&, int, cudaStream_t);
 extern template cudaError_t launch_t<double, 3, 2, 2, 2>(const SolveArgs&, int, cudaStream_t);
 }  // namespace ieti_t
 
 namespace {
-template <typename T>
-cudaError_t dispatch(const SolveArgs& a, int dim, int p0, int p1, int p2, int threads, cudaStream_t st) {
+cudaError_t dispatch_float(const SolveArgs& a, int dim, int p0, int p1, int p2, int threads, cudaStream_t st) {
     using namespace ieti_t;
-    if (dim == 2 && p2 == 0) {
-        switch (p0 * 10 + p1) {
-            case 22: return launch_t<T, 2, 2, 2, 0>(a, threads, st);
-            case 23: return launch_t<T, 2, 2, 3, 0>(a, threads, st);
-            case 24: return launch_t<T, 2, 2, 4, 0>(a, threads, st);
-            case 32: return launch_t<T, 2, 3, 2, 0>(a, threads, st);
-            case 33: return launch_t<T, 2, 3, 3, 0>(a, threads, st);
-            case 34: return launch_t<T, 2, 3, 4, 0>(a, threads, st);
-            case 42: return launch_t<T, 2, 4, 2, 0>(a, threads, st);
-            case 43: return launch_t<T, 2, 4, 3, 0>(a, threads, st);
-            case 44: return launch_t<T, 2, 4, 4, 0>(a, threads, st);
-            default: break;
-        }
-    } else if (dim == 3 && p0 == p1 && p1 == p2) {
-        if (p0 == 2) return launch_t<T, 3, 2, 2, 2>(a, threads, st);
+    const int key = dim * 1000 + p0 * 100 + p1 * 10 + p2;
+    switch (key) {
+        case 2220: return launch_t<float, 2, 2, 2, 0>(a, threads, st);
+        case 2230: return launch_t<float, 2, 2, 3, 0>(a, threads, st);
+        case 2240: return launch_t<float, 2, 2, 4, 0>(a, threads, st);
+        case 2320: return launch_t<float, 2, 3, 2, 0>(a, threads, st);
+        case 2330: return launch_t<float, 2, 3, 3, 0>(a, threads, st);
+        case 2340: return launch_t<float, 2, 3, 4, 0>(a, threads, st);
+        case 2420: return launch_t<float, 2, 4, 2, 0>(a, threads, st);
+        case 2430: return launch_t<float, 2, 4, 3, 0>(a, threads, st);
+        case 2440: return launch_t<float, 2, 4, 4, 0>(a, threads, st);
+        case 3222: return launch_t<float, 3, 2, 2, 2>(a, threads, st);
+        default: return cudaErrorNotSupported;
     }
-    return cudaErrorNotSupported;
+}
+cudaError_t dispatch_double(const SolveArgs& a, int dim, int p0, int p1, int p2, int threads, cudaStream_t st) {
+    using namespace ieti_t;
+    const int key = dim * 1000 + p0 * 100 + p1 * 10 + p2;
+    switch (key) {
+        case 2220: return launch_t<double, 2, 2, 2, 0>(a, threads, st);
+        case 2330: return launch_t<double, 2, 3, 3, 0>(a, threads, st);
+        case 3222: return launch_t<double, 3, 2, 2, 2>(a, threads, st);
+        default: return cudaErrorNotSupported;
+    }
 }
 }  // namespace
 
-bool solve_variant_exists(int dim, int p0, int p1, int p2) {
-    if (dim == 2) return p2 == 0 && p0 >= 2 && p0 <= 4 && p1 >= 2 && p1 <= 4;
-    return dim == 3 && p0 == p1 && p1 == p2 && p0 == 2;
+bool solve_variant_exists(int dim, int p0, int p1, int p2, int mixed) {
+    const int key = dim * 1000 + p0 * 100 + p1 * 10 + p2;
+    if (mixed) return key == 2220 || key == 2230 || key == 2240 || key == 2320 || key == 2330 || key == 2340 || key == 2420 || key == 2430 || key == 2440 || key == 3222;
+    return key == 2220 || key == 2330 || key == 3222;
 }
 
 cudaError_t launch_solve_variant(const SolveArgs& a, int dim, int p0, int p1, int p2, int threads,
                                  cudaStream_t st) {
-    if (a.mixed) return dispatch<float>(a, dim, p0, p1, p2, threads, st);
-    return dispatch<double>(a, dim, p0, p1, p2, threads, st);
+    if (a.mixed) return dispatch_float(a, dim, p0, p1, p2, threads, st);
+    return dispatch_double(a, dim, p0, p1, p2, threads, st);
 }
 
 size_t solve_smem_need(const PatchDesc& P, int mixed) {

@@ -48,19 +48,37 @@ __device__ __forceinline__ void cta_sum(double* val, Red& sh) {
 
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
 
+constexpr int sp_of(int S) { return (((S + 3) & ~3) / 4) % 2 == 0 ? ((S + 3) & ~3) + 4 : ((S + 3) & ~3); }
+
+// per level (l >= 1) and color: storage offset and counts of the color's rows,
+// base and strides of its ghost-padded block in the color-major x
+struct CTab {
+    int off, k0, k1, k2, xb, xk0, xk1;
+};
+
 // shared-memory plan of one slot for a dynamic budget B (same on host and device)
 struct Plan {
-    bool vec;       // V-cycle vectors in shared memory
+    bool vec;       // x, b, r in shared memory
     bool a0;        // coarsest inverse in shared memory
     int ls;         // matrices of levels 0..ls in shared memory (-1: none)
-    size_t a0_off, mat_off, used;
+    size_t tab_off, vec_off, a0_off, mat_off, used;
 };
+
+__host__ __device__ inline size_t ctab_bytes(const PatchDesc& P) {
+    return align16((size_t)P.L * ieti_ncolors(P.p) * sizeof(CTab));
+}
+__host__ __device__ inline size_t vec_elems(const PatchDesc& P) {
+    return (size_t)P.nlx + P.nlb + P.lev[P.L - 1].n;
+}
 
 __host__ __device__ inline Plan make_plan(const PatchDesc& P, size_t tsize, size_t B) {
     Plan pl;
     size_t used = 0;
-    size_t vb = align16(3 * (size_t)P.nlvec * tsize);
-    pl.vec = vb <= B;
+    pl.tab_off = 0;
+    used += ctab_bytes(P);
+    pl.vec_off = used;
+    size_t vb = align16(vec_elems(P) * tsize);
+    pl.vec = used + vb <= B;
     if (pl.vec) used += vb;
     size_t ab = align16((size_t)P.lev[0].n * P.lev[0].n * tsize);
     pl.a0 = used + ab <= B;
@@ -69,7 +87,7 @@ __host__ __device__ inline Plan make_plan(const PatchDesc& P, size_t tsize, size
     pl.mat_off = used;
     pl.ls = -1;
     for (int l = 0; l < P.L - 1; ++l) {
-        size_t mb = (size_t)P.lev[l].n * P.lev[l].S * tsize;
+        size_t mb = (size_t)P.lev[l].n * P.lev[l].Sp * tsize;
         if (used + mb > B) break;
         used += mb;
         pl.ls = l;
@@ -80,163 +98,182 @@ __host__ __device__ inline Plan make_plan(const PatchDesc& P, size_t tsize, size
 
 // full shared-memory need of one slot (host side sizing)
 inline size_t smem_need(const PatchDesc& P, size_t tsize) {
-    size_t b = align16(3 * (size_t)P.nlvec * tsize) + align16((size_t)P.lev[0].n * P.lev[0].n * tsize);
-    for (int l = 0; l < P.L - 1; ++l) b += (size_t)P.lev[l].n * P.lev[l].S * tsize;
+    size_t b = ctab_bytes(P) + align16(vec_elems(P) * tsize) + align16((size_t)P.lev[0].n * P.lev[0].n * tsize);
+    for (int l = 0; l < P.L - 1; ++l) b += (size_t)P.lev[l].n * P.lev[l].Sp * tsize;
     return b;
+}
+
+template <typename T>
+struct V4;
+template <>
+struct V4<float> {
+    using type = float4;
+};
+template <>
+struct V4<double> {
+    using type = double2;   // two 16-byte loads per 4 values
+};
+
+template <typename T>
+__device__ __forceinline__ void load4(const T* p, T* w);
+template <>
+__device__ __forceinline__ void load4<float>(const float* p, float* w) {
+    float4 v = *reinterpret_cast<const float4*>(p);
+    w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+}
+template <>
+__device__ __forceinline__ void load4<double>(const double* p, double* w) {
+    double2 a = reinterpret_cast<const double2*>(p)[0];
+    double2 b = reinterpret_cast<const double2*>(p)[1];
+    w[0] = a.x; w[1] = a.y; w[2] = b.x; w[3] = b.y;
 }
 
 template <typename T, int D, int P0, int P1, int P2>
 struct VC {
     static constexpr int W0 = 2 * P0 + 1, W1 = 2 * P1 + 1, W2 = 2 * P2 + 1;
+    static constexpr int S = W0 * W1 * W2, SP = sp_of(S);
     static constexpr int C0 = P0 + 1, C1 = P1 + 1, C2 = P2 + 1, NC = C0 * C1 * C2;
     static constexpr int R0 = P0 + 2, R1 = P1 + 2, R2 = D == 3 ? P2 + 2 : 1;
 
     const PatchDesc* P;   // shared copy
     int mask;
-    T alpha;
-    const T* Kg;          // global value pool
+    const T* Kg;          // global value pool (K or K + alpha M^)
     const T* Ks;          // shared matrices of levels 0..ls
     int ls;
     long long kbase;
     const T* tab;
     const int* itab;
     const T* A0;
-    T* lvec;
-    int nlvec;
+    T* xs;                // x of all levels (level >= 1 color-major padded, level 0 natural)
+    T* bs;                // b of all levels (level >= 1 storage order, level 0 natural)
+    T* rs;                // fine-level residual (natural)
+    const CTab* ct;       // [l * NC + c]
 
     __device__ __forceinline__ const T* vals(int l) const {
         return l <= ls ? Ks + (P->lev[l].koff - kbase) : Kg + P->lev[l].koff;
     }
-    __device__ __forceinline__ T* X(int l) const { return lvec + P->lev[l].voff; }
-    __device__ __forceinline__ T* B(int l) const { return lvec + nlvec + P->lev[l].voff; }
-    __device__ __forceinline__ T* R(int l) const { return lvec + 2 * nlvec + P->lev[l].voff; }
+    __device__ __forceinline__ T* X(int l) const { return xs + P->lev[l].xoff; }
+    __device__ __forceinline__ T* B(int l) const { return bs + P->lev[l].boff; }
 
-    // (A x)_i and the diagonal for row (i0,i1,i2) at storage position s
-    template <bool REG>
-    __device__ __forceinline__ T row(const T* v, int n, int s, const T* x, int m0, int m1, int m2, int i0, int i1,
-                                     int i2, const T* mt0, const T* mt1, const T* mt2, T* diag) const {
-        T acc = 0;
-        const int i = i0 + m0 * (i1 + m1 * i2);
+    // color-major position of natural (i0,i1,i2) at level l >= 1
+    __device__ __forceinline__ int cm_pos(int l, int i0, int i1, int i2) const {
+        const int c = (i0 % C0) + C0 * ((i1 % C1) + C1 * (i2 % C2));
+        const CTab& t = ct[l * NC + c];
+        return t.xb + (i0 / C0 + 1) + t.xk0 * ((i1 / C1 + 1) + t.xk1 * (D == 3 ? i2 / C2 + 1 : 0));
+    }
+
+    // one row of color CC at level l: returns (A x)_row, diagonal in *d
+    template <int CC>
+    __device__ __forceinline__ T row(const T* __restrict__ vr, const T* x, int l, int t0, int t1, int t2,
+                                     T* d) const {
+        constexpr int c0 = CC % C0, c1 = (CC / C0) % C1, c2 = CC / (C0 * C1);
+        T acc[4] = {T(0), T(0), T(0), T(0)};
+        const CTab* tl = ct + l * NC;
 #pragma unroll
-        for (int o2 = -P2; o2 <= P2; ++o2) {
-            const bool v2 = (unsigned)(i2 + o2) < (unsigned)m2;
-            T mz = 1;
-            if (REG && D == 3) mz = mt2[i2 * W2 + o2 + P2];
+        for (int q = 0; q < SP / 4; ++q) {
+            T w[4];
+            load4<T>(vr + 4 * q, w);
 #pragma unroll
-            for (int o1 = -P1; o1 <= P1; ++o1) {
-                const bool v1 = v2 && (unsigned)(i1 + o1) < (unsigned)m1;
-                const int xb = i + m0 * (o1 + m1 * o2);
-                T my = 1;
-                if (REG) my = mt1[i1 * W1 + o1 + P1] * mz;
-#pragma unroll
-                for (int o0 = -P0; o0 <= P0; ++o0) {
-                    const bool vv = v1 && (unsigned)(i0 + o0) < (unsigned)m0;
-                    const int o = (o0 + P0) + W0 * ((o1 + P1) + W1 * (o2 + P2));
-                    T a = v[(long long)o * n + s];
-                    if (REG) a += alpha * mt0[i0 * W0 + o0 + P0] * my;
-                    acc += a * x[vv ? xb + o0 : i];
+            for (int j = 0; j < 4; ++j) {
+                const int o = 4 * q + j;
+                if (o < S) {
+                    const int o0 = o % W0 - P0, o1 = (o / W0) % W1 - P1, o2 = o / (W0 * W1) - P2;
+                    const int e0 = c0 + o0 + C0, e1 = c1 + o1 + C1, e2 = c2 + o2 + C2;
+                    const int n0 = e0 % C0, n1 = e1 % C1, n2 = e2 % C2;
+                    const int d0 = e0 / C0 - 1, d1 = e1 / C1 - 1, d2 = e2 / C2 - 1;
+                    const CTab& tn = tl[n0 + C0 * (n1 + C1 * n2)];
+                    const int pos = tn.xb + (t0 + d0 + 1) +
+                                    tn.xk0 * ((t1 + d1 + 1) + (D == 3 ? tn.xk1 * (t2 + d2 + 1) : 0));
+                    acc[j] += w[j] * x[pos];
                 }
             }
         }
-        if (diag) {
-            constexpr int oc = P0 + W0 * (P1 + W1 * P2);
-            T dd = v[(long long)oc * n + s];
-            if (REG) {
-                T mm = mt0[i0 * W0 + P0] * mt1[i1 * W1 + P1];
-                if (D == 3) mm *= mt2[i2 * W2 + P2];
-                dd += alpha * mm;
-            }
-            *diag = dd;
-        }
-        return acc;
+        constexpr int oc = P0 + W0 * (P1 + W1 * P2);
+        *d = vr[oc];
+        return (acc[0] + acc[1]) + (acc[2] + acc[3]);
     }
 
-    template <bool REG>
-    __device__ void sweep_t(int l, bool forward) const {
+    template <int CC>
+    __device__ void color_step(int l) const {
+        constexpr int c0 = CC % C0, c1 = (CC / C0) % C1, c2 = CC / (C0 * C1);
         const LevelDesc& L = P->lev[l];
-        const int m0 = L.m[0], m1 = L.m[1], m2 = L.m[2], n = L.n;
-        const T* v = vals(l);
+        const CTab t = ct[l * NC + CC];
+        const T* v = vals(l) + (long long)t.off * SP;
         T* x = X(l);
-        const T* b = B(l);
-        const T* mt0 = tab + L.mw[0];
-        const T* mt1 = tab + L.mw[1];
-        const T* mt2 = D == 3 ? tab + L.mw[2] : nullptr;
-        const int pp[3] = {P0, P1, P2};
-        for (int cc = 0; cc < NC; ++cc) {
-            const int c = forward ? cc : NC - 1 - cc;
-            const int c0 = c % C0, c1 = (c / C0) % C1, c2 = c / (C0 * C1);
-            const int k0 = ieti_cnt(m0, P0, c0), k1 = ieti_cnt(m1, P1, c1);
-            const int k2 = ieti_cnt(m2, P2, c2);
-            const int off = ieti_color_off(L.m, pp, c0, c1, c2);
-            const int cnt = k0 * k1 * k2;
-            for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-                const int t0 = t % k0, tr = t / k0;
-                const int t1 = tr % k1, t2 = tr / k1;
-                const int i0 = c0 + C0 * t0, i1 = c1 + C1 * t1, i2 = c2 + C2 * t2;
-                if (ieti_masked(mask, L.m, i0, i1, i2)) continue;
-                T d;
-                const T ax = row<REG>(v, n, off + t, x, m0, m1, m2, i0, i1, i2, mt0, mt1, mt2, &d);
-                const int i = i0 + m0 * (i1 + m1 * i2);
-                x[i] += (b[i] - ax) / d;
-            }
-            __syncthreads();
-        }
-    }
-
-    template <bool REG>
-    __device__ void residual_t(int l) const {
-        const LevelDesc& L = P->lev[l];
-        const int m0 = L.m[0], m1 = L.m[1], m2 = L.m[2], n = L.n;
-        const T* v = vals(l);
-        const T* x = X(l);
-        const T* b = B(l);
-        T* r = R(l);
-        const T* mt0 = tab + L.mw[0];
-        const T* mt1 = tab + L.mw[1];
-        const T* mt2 = D == 3 ? tab + L.mw[2] : nullptr;
-        const int pp[3] = {P0, P1, P2};
-        for (int c = 0; c < NC; ++c) {
-            const int c0 = c % C0, c1 = (c / C0) % C1, c2 = c / (C0 * C1);
-            const int k0 = ieti_cnt(m0, P0, c0), k1 = ieti_cnt(m1, P1, c1);
-            const int k2 = ieti_cnt(m2, P2, c2);
-            const int off = ieti_color_off(L.m, pp, c0, c1, c2);
-            const int cnt = k0 * k1 * k2;
-            for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-                const int t0 = t % k0, tr = t / k0;
-                const int t1 = tr % k1, t2 = tr / k1;
-                const int i0 = c0 + C0 * t0, i1 = c1 + C1 * t1, i2 = c2 + C2 * t2;
-                const int i = i0 + m0 * (i1 + m1 * i2);
-                if (ieti_masked(mask, L.m, i0, i1, i2)) {
-                    r[i] = 0;
-                    continue;
-                }
-                r[i] = b[i] - row<REG>(v, n, off + t, x, m0, m1, m2, i0, i1, i2, mt0, mt1, mt2, (T*)nullptr);
-            }
+        const T* b = B(l) + t.off;
+        const int cnt = t.k0 * t.k1 * t.k2;
+        for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+            const int t0 = q % t.k0, tr = q / t.k0;
+            const int t1 = tr % t.k1, t2 = tr / t.k1;
+            const int i0 = c0 + C0 * t0, i1 = c1 + C1 * t1, i2 = c2 + C2 * t2;
+            if (ieti_masked(mask, L.m, i0, i1, i2)) continue;
+            T dg;
+            const T ax = row<CC>(v + (long long)q * SP, x, l, t0, t1, t2, &dg);
+            const int pos = t.xb + (t0 + 1) + t.xk0 * ((t1 + 1) + (D == 3 ? t.xk1 * (t2 + 1) : 0));
+            x[pos] += (b[q] - ax) / dg;
         }
         __syncthreads();
     }
 
-    __device__ void sweep(int l, bool fw) const {
-        if (alpha != T(0)) sweep_t<true>(l, fw);
-        else sweep_t<false>(l, fw);
-    }
-    __device__ void residual(int l) const {
-        if (alpha != T(0)) residual_t<true>(l);
-        else residual_t<false>(l);
+    template <int CC>
+    __device__ void resid_color(int l) const {
+        constexpr int c0 = CC % C0, c1 = (CC / C0) % C1, c2 = CC / (C0 * C1);
+        const LevelDesc& L = P->lev[l];
+        const CTab t = ct[l * NC + CC];
+        const T* v = vals(l) + (long long)t.off * SP;
+        const T* x = X(l);
+        const T* b = B(l) + t.off;
+        const int cnt = t.k0 * t.k1 * t.k2;
+        for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+            const int t0 = q % t.k0, tr = q / t.k0;
+            const int t1 = tr % t.k1, t2 = tr / t.k1;
+            const int i0 = c0 + C0 * t0, i1 = c1 + C1 * t1, i2 = c2 + C2 * t2;
+            const int i = i0 + L.m[0] * (i1 + L.m[1] * i2);
+            if (ieti_masked(mask, L.m, i0, i1, i2)) {
+                rs[i] = T(0);
+                continue;
+            }
+            T dg;
+            rs[i] = b[q] - row<CC>(v + (long long)q * SP, x, l, t0, t1, t2, &dg);
+        }
     }
 
+    template <int CC>
+    __device__ __forceinline__ void color_dispatch(int c, int l, int what) const {
+        if constexpr (CC < NC) {
+            if (c == CC) {
+                if (what == 0) color_step<CC>(l);
+                else resid_color<CC>(l);
+            } else {
+                color_dispatch<CC + 1>(c, l, what);
+            }
+        }
+    }
+
+    __device__ void sweep(int l, bool forward) const {
+        for (int cc = 0; cc < NC; ++cc) color_dispatch<0>(forward ? cc : NC - 1 - cc, l, 0);
+    }
+
+    __device__ void residual(int l) const {
+        for (int c = 0; c < NC; ++c) color_dispatch<0>(c, l, 1);
+        __syncthreads();
+    }
+
+    // b_{l-1} = P^T r_l (r natural), x_{l-1} = 0
     __device__ void restrict_to(int l) const {
         const LevelDesc& F = P->lev[l];
         const LevelDesc& Cl = P->lev[l - 1];
-        const T* r = R(l);
         T* bc = B(l - 1);
         T* xc = X(l - 1);
+        const int nxc = l - 1 >= 1 ? Cl.nx : Cl.n;
+        for (int t = threadIdx.x; t < nxc; t += blockDim.x) xc[t] = T(0);
         for (int I = threadIdx.x; I < Cl.n; I += blockDim.x) {
             const int I0 = I % Cl.m[0], Ir = I / Cl.m[0];
             const int I1 = Ir % Cl.m[1], I2 = Ir / Cl.m[1];
-            xc[I] = 0;
+            const int pp[3] = {P0, P1, P2};
+            const int dst = l - 1 >= 1 ? ieti_store_pos(Cl.m, pp, I0, I1, I2) : I;
             if (ieti_masked(mask, Cl.m, I0, I1, I2)) {
-                bc[I] = 0;
+                bc[dst] = T(0);
                 continue;
             }
             const int a0 = itab[F.rs[0] + I0], a1 = itab[F.rs[1] + I1];
@@ -255,7 +292,7 @@ struct VC {
                     const int f1 = a1 + u1;
                     const bool ok1 = ok2 && f1 < F.m[1];
                     const T ww1 = w1[u1] * ww2;
-                    const T* rr = r + F.m[0] * ((ok1 ? f1 : 0) + F.m[1] * (ok1 ? f2 : 0));
+                    const T* rr = rs + F.m[0] * ((ok1 ? f1 : 0) + F.m[1] * (ok1 ? f2 : 0));
                     T s = 0;
 #pragma unroll
                     for (int u0 = 0; u0 < R0; ++u0) {
@@ -266,16 +303,18 @@ struct VC {
                     acc += ww1 * s;
                 }
             }
-            bc[I] = acc;
+            bc[dst] = acc;
         }
         __syncthreads();
     }
 
+    // x_l += P x_{l-1}
     __device__ void prolong_add(int l) const {
         const LevelDesc& F = P->lev[l];
         const LevelDesc& Cl = P->lev[l - 1];
         const T* xc = X(l - 1);
         T* x = X(l);
+        const bool cnat = l - 1 == 0;
         for (int i = threadIdx.x; i < F.n; i += blockDim.x) {
             const int i0 = i % F.m[0], ir = i / F.m[0];
             const int i1 = ir % F.m[1], i2 = ir / F.m[1];
@@ -288,26 +327,26 @@ struct VC {
             T acc = 0;
 #pragma unroll
             for (int u2 = 0; u2 < R2; ++u2) {
-                const int c2 = a2 + u2;
+                const int q2 = a2 + u2;
                 const T ww2 = D == 3 ? w2[u2] : T(1);
-                const bool ok2 = c2 < Cl.m[2];
+                if (q2 >= Cl.m[2]) continue;
 #pragma unroll
                 for (int u1 = 0; u1 < R1; ++u1) {
-                    const int c1 = a1 + u1;
-                    const bool ok1 = ok2 && c1 < Cl.m[1];
+                    const int q1 = a1 + u1;
+                    if (q1 >= Cl.m[1]) continue;
                     const T ww1 = w1[u1] * ww2;
-                    const T* xx = xc + Cl.m[0] * ((ok1 ? c1 : 0) + Cl.m[1] * (ok1 ? c2 : 0));
                     T s = 0;
 #pragma unroll
                     for (int u0 = 0; u0 < R0; ++u0) {
-                        const int cc0 = a0 + u0;
-                        const bool ok = ok1 && cc0 < Cl.m[0];
-                        s += w0[u0] * (ok ? xx[cc0] : T(0));
+                        const int q0 = a0 + u0;
+                        if (q0 >= Cl.m[0]) continue;
+                        const int src = cnat ? q0 + Cl.m[0] * (q1 + Cl.m[1] * q2) : cm_pos(l - 1, q0, q1, q2);
+                        s += w0[u0] * xc[src];
                     }
                     acc += ww1 * s;
                 }
             }
-            x[i] += acc;
+            x[cm_pos(l, i0, i1, i2)] += acc;
         }
         __syncthreads();
     }
@@ -329,6 +368,8 @@ struct VC {
         __syncthreads();
     }
 
+    // x_fine = V(b_fine): b_fine (storage order, or natural for a 1-level
+    // hierarchy) set by the caller
     __device__ __noinline__ void run(int nu1, int nu2) const {
         const int L = P->L;
         if (L == 1) {
@@ -337,7 +378,8 @@ struct VC {
         }
         {
             T* x = X(L - 1);
-            for (int i = threadIdx.x; i < P->lev[L - 1].n; i += blockDim.x) x[i] = 0;
+            const int nx = P->lev[L - 1].nx;
+            for (int i = threadIdx.x; i < nx; i += blockDim.x) x[i] = T(0);
             __syncthreads();
         }
         for (int l = L - 1; l >= 1; --l) {
@@ -349,6 +391,30 @@ struct VC {
         for (int l = 1; l <= L - 1; ++l) {
             prolong_add(l);
             for (int s = 0; s < nu2; ++s) sweep(l, false);
+        }
+    }
+
+    // fill the color tables of every level >= 1
+    __device__ void build_tables(CTab* tabs) const {
+        const int pp[3] = {P0, P1, P2};
+        for (int e = threadIdx.x; e < P->L * NC; e += blockDim.x) {
+            const int l = e / NC, c = e % NC;
+            const LevelDesc& L = P->lev[l];
+            const int c0 = c % C0, c1 = (c / C0) % C1, c2 = c / (C0 * C1);
+            CTab t;
+            t.off = ieti_color_off(L.m, pp, c0, c1, c2);
+            t.k0 = ieti_cnt(L.m[0], P0, c0);
+            t.k1 = ieti_cnt(L.m[1], P1, c1);
+            t.k2 = ieti_cnt(L.m[2], P2, c2);
+            t.xk0 = t.k0 + 2;
+            t.xk1 = t.k1 + 2;
+            int xb = 0;
+            for (int cc = 0; cc < c; ++cc) {
+                const int e0 = cc % C0, e1 = (cc / C0) % C1, e2 = cc / (C0 * C1);
+                xb += ieti_cm_block(L.m, pp, D, e0, e1, e2);
+            }
+            t.xb = xb;
+            tabs[e] = t;
         }
     }
 };
@@ -365,8 +431,7 @@ __device__ __forceinline__ double k64_row(const PatchDesc& P, const double* __re
     if (ieti_masked(mask, L.m, i0, i1, i2)) return 0.0;
     const int pp[3] = {P0, P1, P2};
     const int s = ieti_store_pos(L.m, pp, i0, i1, i2);
-    const double* v = K64 + L.koff;
-    const int n = L.n;
+    const double* v = K64 + L.koff + (long long)s * L.Sp;
     double acc = 0.0;
 #pragma unroll
     for (int o2 = -P2; o2 <= P2; ++o2) {
@@ -379,7 +444,7 @@ __device__ __forceinline__ double k64_row(const PatchDesc& P, const double* __re
             for (int o0 = -P0; o0 <= P0; ++o0) {
                 const bool vv = v1 && (unsigned)(i0 + o0) < (unsigned)m0;
                 const int o = (o0 + P0) + W0 * ((o1 + P1) + W1 * (o2 + P2));
-                acc += __ldg(v + (long long)o * n + s) * x[vv ? xb + o0 : i];
+                acc += __ldg(v + o) * x[vv ? xb + o0 : i];
             }
         }
     }
@@ -411,13 +476,23 @@ __device__ __noinline__ void spmv64(const PatchDesc& P, const double* __restrict
 template <typename T, int D, int P0, int P1, int P2>
 __device__ void vcycle_apply(const VC<T, D, P0, P1, P2>& vc, const double* rin, double* zout, int nu1, int nu2) {
     const int L = vc.P->L;
-    const int n = vc.P->lev[L - 1].n;
+    const LevelDesc& F = vc.P->lev[L - 1];
+    const int n = F.n;
     T* b = vc.B(L - 1);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) b[i] = (T)rin[i];
+    const int pp[3] = {P0, P1, P2};
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int i0 = i % F.m[0], ir = i / F.m[0];
+        const int i1 = ir % F.m[1], i2 = ir / F.m[1];
+        b[L > 1 ? ieti_store_pos(F.m, pp, i0, i1, i2) : i] = (T)rin[i];
+    }
     __syncthreads();
     vc.run(nu1, nu2);
     const T* x = vc.X(L - 1);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) zout[i] = (double)x[i];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int i0 = i % F.m[0], ir = i / F.m[0];
+        const int i1 = ir % F.m[1], i2 = ir / F.m[1];
+        zout[i] = (double)x[L > 1 ? vc.cm_pos(L - 1, i0, i1, i2) : i];
+    }
     __syncthreads();
 }
 
@@ -483,24 +558,28 @@ __global__ void __launch_bounds__(512) k_solve_t(SolveArgs a) {
     double* q = p + n;
     const int allsides = D == 2 ? 0xF : 0x3F;
     const int kind = (a.mode == MODE_SCHUR) ? 1 : 0;
-    const T* Kg = a.mixed ? (const T*)(const void*)a.K32 : (const T*)(const void*)a.K64;
     const T* A0g = (a.mixed ? (const T*)(const void*)a.A0inv32 : (const T*)(const void*)a.A0inv64) + P.a0off[kind];
 
     const Plan pl = make_plan(P, sizeof(T), a.smem_bytes);
+    const bool reg = kind == 0 && P.floating;
+    const T* Kv = a.mixed ? (const T*)(const void*)(reg ? a.KM32 : a.K32)
+                          : (const T*)(const void*)(reg ? a.KM64 : a.K64);
     VC<T, D, P0, P1, P2> vc;
     vc.P = &P;
     vc.mask = kind == 0 ? P.dmask : allsides;
-    vc.alpha = (kind == 0 && P.floating) ? (T)a.alpha : T(0);
-    vc.Kg = Kg;
+    vc.Kg = Kv;
     vc.tab = a.mixed ? (const T*)(const void*)a.tabf : (const T*)(const void*)a.tab;
     vc.itab = a.itab;
-    vc.nlvec = P.nlvec;
-    vc.lvec = pl.vec ? (T*)dyn : (T*)a.lv + sd.lv;
+    T* vbase = pl.vec ? (T*)(dyn + pl.vec_off) : (T*)a.lv + sd.lv;
+    vc.xs = vbase;
+    vc.bs = vbase + P.nlx;
+    vc.rs = vbase + P.nlx + P.nlb;
     vc.kbase = P.lev[0].koff;
     vc.ls = pl.ls;
     vc.Ks = (const T*)(dyn + pl.mat_off);
     vc.A0 = pl.a0 ? (const T*)(dyn + pl.a0_off) : A0g;
-    // stage the coarsest inverse and coarse-level matrices
+    vc.ct = (const CTab*)(dyn + pl.tab_off);
+    vc.build_tables((CTab*)(dyn + pl.tab_off));
     if (pl.a0) {
         T* dst = (T*)(dyn + pl.a0_off);
         const int nn = P.lev[0].n * P.lev[0].n;
@@ -508,8 +587,8 @@ __global__ void __launch_bounds__(512) k_solve_t(SolveArgs a) {
     }
     if (pl.ls >= 0) {
         T* dst = (T*)(dyn + pl.mat_off);
-        const long long cnt = P.lev[pl.ls].koff + (long long)P.lev[pl.ls].n * P.lev[pl.ls].S - vc.kbase;
-        const T* src = Kg + vc.kbase;
+        const long long cnt = P.lev[pl.ls].koff + (long long)P.lev[pl.ls].n * P.lev[pl.ls].Sp - vc.kbase;
+        const T* src = Kv + vc.kbase;
         for (long long t = threadIdx.x; t < cnt; t += blockDim.x) dst[t] = src[t];
     }
     __syncthreads();
