@@ -25,9 +25,15 @@ def nvcc():
     return cand if os.path.exists(cand) else "nvcc"
 
 
+def _flags():
+    # IETIDP_DEBUG_BOUNDS=1 builds the self-checking variant of the local
+    # solver (every computed index is checked against its buffer)
+    return FLAGS + (["-DIETI_DEBUG_BOUNDS"] if os.environ.get("IETIDP_DEBUG_BOUNDS") == "1" else [])
+
+
 def _compile(src):
     obj = os.path.join(OUT, os.path.splitext(src)[0] + ".o")
-    cmd = [nvcc(), *ARCH, *FLAGS, "-c", os.path.join(SRC, src), "-o", obj]
+    cmd = [nvcc(), *ARCH, *_flags(), "-c", os.path.join(SRC, src), "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr}")

@@ -6,15 +6,15 @@
 // xi_r = 1; a masked side's functions are removed from the operator (their
 // rows are skipped, their vector entries stay 0).
 //
-// Banded stiffness storage: for a level with n functions and stencil size
-// S = prod_r (2 p_r + 1), values[s * Sp + o] holds K(i, i + offset(o)) where s
-// is the storage position of row i and Sp >= S the padded row length (a
-// multiple of 4 with Sp/4 odd, so that 16-byte row loads by consecutive
-// threads fall in distinct shared-memory bank groups).  Rows are stored color
-// by color (color c = sum_r (i_r mod (p_r+1)) * stride_r, the multicolor
-// Gauss-Seidel classes), and within a color in lexicographic order of
-// t_r = i_r / (p_r+1): the rows one color step touches are one contiguous
-// block.  Out-of-grid stencil entries are stored as 0.
+// Banded stiffness storage ("color-blocked SoA"): rows are grouped by
+// Gauss-Seidel color (color c = sum_r (i_r mod (p_r+1)) * stride_r), and
+// within a color numbered q in lexicographic order of t_r = i_r / (p_r+1).
+// Color c owns one contiguous block of cnt_c * S values (S = prod_r (2p_r+1)
+// stencil entries) starting at off_c * S, laid out offset-major:
+// K(i, i + offset(o)) sits at off_c * S + o * cnt_c + q.  A warp working on
+// one color reads each stencil diagonal with unit stride (coalesced in
+// global memory, bank-conflict free in shared memory), and the values one
+// color step needs form one contiguous range.  Out-of-grid entries are 0.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -89,11 +89,15 @@ __host__ __device__ inline int ieti_store_pos(const int* m, const int* p, int i0
 
 __host__ __device__ inline int ieti_ncolors(const int* p) { return (p[0] + 1) * (p[1] + 1) * (p[2] + 1); }
 
-// padded row length: multiple of 4 with an odd number of 4-groups
-__host__ __device__ inline int ieti_sp(int S) {
-    int sp = (S + 3) & ~3;
-    if ((sp / 4) % 2 == 0) sp += 4;
-    return sp;
+// row length of the value arrays (no padding in the color-blocked layout)
+__host__ __device__ inline int ieti_sp(int S) { return S; }
+
+// position of K(i, i + offset(o)) in a level's value array
+__host__ __device__ inline long long ieti_val_pos(const int* m, const int* p, int S, int i0, int i1, int i2, int o) {
+    int c0 = i0 % (p[0] + 1), c1 = i1 % (p[1] + 1), c2 = i2 % (p[2] + 1);
+    int k0 = ieti_cnt(m[0], p[0], c0), k1 = ieti_cnt(m[1], p[1], c1), k2 = ieti_cnt(m[2], p[2], c2);
+    int q = i0 / (p[0] + 1) + k0 * (i1 / (p[1] + 1) + k1 * (i2 / (p[2] + 1)));
+    return (long long)ieti_color_off(m, p, c0, c1, c2) * S + (long long)o * (k0 * k1 * k2) + q;
 }
 
 // color-major, ghost-padded vector layout of the specialised solver: color c

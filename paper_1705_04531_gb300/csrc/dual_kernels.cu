@@ -106,7 +106,6 @@ __device__ __forceinline__ double k64_apply_row(const PatchDesc& P, const double
     const LevelDesc& L = P.lev[P.L - 1];
     int i0 = i % L.m[0], i1 = (i / L.m[0]) % L.m[1], i2 = i / (L.m[0] * L.m[1]);
     if (ieti_masked(P.dmask, L.m, i0, i1, i2)) return 0.0;
-    int s = ieti_store_pos(L.m, P.p, i0, i1, i2);
     const double* vals = K64 + L.koff;
     int lo0 = max(-P.p[0], -i0), hi0 = min(P.p[0], L.m[0] - 1 - i0);
     int lo1 = max(-P.p[1], -i1), hi1 = min(P.p[1], L.m[1] - 1 - i1);
@@ -117,7 +116,8 @@ __device__ __forceinline__ double k64_apply_row(const PatchDesc& P, const double
         for (int o1 = lo1; o1 <= hi1; ++o1) {
             int ob = ((o2 + P.p[2]) * w1 + (o1 + P.p[1])) * w0 + P.p[0];
             int xb = i0 + L.m[0] * ((i1 + o1) + L.m[1] * (i2 + o2));
-            for (int o0 = lo0; o0 <= hi0; ++o0) acc += vals[(long long)s * L.Sp + ob + o0] * x[xb + o0];
+            for (int o0 = lo0; o0 <= hi0; ++o0)
+                acc += vals[ieti_val_pos(L.m, P.p, L.S, i0, i1, i2, ob + o0)] * x[xb + o0];
         }
     return acc;
 }

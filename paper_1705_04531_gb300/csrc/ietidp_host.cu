@@ -161,6 +161,7 @@ struct ietidp_handle {
     void* lv = nullptr;
     int* its = nullptr;
     int* flags = nullptr;
+    int* dbg = nullptr;       // self-check record of debug builds (6 ints)
     long long* vst = nullptr;     // [0..4] Neumann-type stats, [8..12] basis stats
     // torn buffers
     double *gF = nullptr, *uF = nullptr, *vS = nullptr, *wS = nullptr, *gR = nullptr, *tmp = nullptr;
@@ -548,6 +549,7 @@ static int run_solve(ietidp_handle* h, int mode, const std::vector<SlotGroup>& g
     a.alpha = h->opt.alpha_reg;
     a.ncycles = h->opt.dirichlet_vcycles;
     a.vstats = vst;
+    a.dbg = h->dbg;
     bool timed = mode == MODE_NEUMANN && h->nev_used + 2 <= (int)h->ev.size();
     if (timed) cudaEventRecord(h->ev[h->nev_used], h->st);
     if (groups.size() == 1) {
@@ -897,6 +899,8 @@ extern "C" int ietidp_setup(const iga_problem* P, const ietidp_options* opt_in, 
     CKH(h->mem.alloc(&h->upi, npi));
     CKH(h->mem.alloc(&h->uloc, h->nrows));
     CKH(h->mem.alloc(&h->flags, 1));
+    CKH(h->mem.alloc(&h->dbg, 8));
+    CUH(cudaMemsetAsync(h->dbg, 0, sizeof(int) * 8, st));
     CKH(h->mem.alloc(&h->vst, 16));
     CUH(cudaMemsetAsync(h->flags, 0, sizeof(int), st));
     CUH(cudaMemsetAsync(h->vst, 0, sizeof(long long) * 16, st));
@@ -1043,6 +1047,7 @@ extern "C" int ietidp_setup(const iga_problem* P, const ietidp_options* opt_in, 
     // ---- primal basis (Eq. 6) ---------------------------------------------
     if (nslot_basis > 0) {
         CHK(run_solve(h, MODE_BASIS, h->gbasis, nullptr, nullptr, opt.tol_basis, opt.maxit_inner, h->vst + 8));
+        CUH(cudaStreamSynchronize(st));
         std::vector<int> its(nslot_basis);
         CUH(cudaMemcpyAsync(its.data(), h->its, sizeof(int) * nslot_basis, cudaMemcpyDeviceToHost, st));
         CUH(cudaStreamSynchronize(st));
@@ -1054,6 +1059,15 @@ extern "C" int ietidp_setup(const iga_problem* P, const ietidp_options* opt_in, 
         h->basis_it_avg = (double)s / nslot_basis;
         int fl = 0;
         CUH(cudaMemcpy(&fl, h->flags, sizeof(int), cudaMemcpyDeviceToHost));
+        {
+            int dbg[8];
+            CUH(cudaMemcpy(dbg, h->dbg, sizeof(dbg), cudaMemcpyDeviceToHost));
+            if (dbg[0] != 0)
+                return bail(fail(IETIDP_E_CUDA, "self-check: " + std::to_string(dbg[0]) + " bad accesses, first at site " +
+                                                    std::to_string(dbg[1]) + " index " + std::to_string(dbg[2]) +
+                                                    " limit " + std::to_string(dbg[3]) + " block " +
+                                                    std::to_string(dbg[4]) + " thread " + std::to_string(dbg[5])));
+        }
         if (fl & IETI_FLAG_BREAKDOWN) return bail(fail(IETIDP_E_BREAKDOWN, "CG breakdown in the primal basis"));
         if (fl & IETI_FLAG_NOT_CONVERGED)
             return bail(fail(IETIDP_E_NOT_CONVERGED, "primal basis solves did not converge"));

@@ -108,6 +108,7 @@ struct SolveArgs {
     int ncycles;               // Schur: V-cycles; V-cycle mode: cycles
     long long* vstats;         // [0] V-cycles, [1] V-cycle fine dofs (atomically added)
     size_t smem_bytes;         // dynamic shared memory of the launch (specialised kernels)
+    int* dbg;                  // self-check record (debug builds only)
 };
 
 // generic kernel (degrees known at run time only)

@@ -249,7 +249,6 @@ __global__ void k_stiffness(SetupArgs a, long long total_rows) {
             rem /= w;
             jj[r] = ii[r] + oo[r];
         }
-        int s = ieti_store_pos(F.m, P.p, ii[0], ii[1], ii[2]);
         bool inside = true;
         for (int r = 0; r < 3; ++r) inside &= (jj[r] >= 0 && jj[r] < F.m[r]);
         double acc = 0.0;
@@ -305,7 +304,7 @@ __global__ void k_stiffness(SetupArgs a, long long total_rows) {
                                     }
                                 }
         }
-        a.K64[F.koff + (long long)s * F.Sp + o] = acc;
+        a.K64[F.koff + ieti_val_pos(F.m, P.p, F.S, ii[0], ii[1], ii[2], o)] = acc;
     }
 }
 
@@ -488,7 +487,6 @@ __global__ void k_galerkin(const PatchDesc* pd, const int* plist, int depth, dou
             Jj[r] = Ii[r] + oo[r];
             inside &= (Jj[r] >= 0 && Jj[r] < C.m[r]);
         }
-        int s = ieti_store_pos(C.m, P.p, Ii[0], Ii[1], Ii[2]);
         double acc = 0.0;
         if (inside) {
             int W[3], ai0[3], bi0[3];
@@ -518,7 +516,6 @@ __global__ void k_galerkin(const PatchDesc* pd, const int* plist, int depth, dou
                             if (ok) pa *= wa[r][tt[r]];
                         }
                         if (!ok || pa == 0.0) continue;
-                        int sa = ieti_store_pos(F.m, P.p, a[0], a[1], a[2]);
                         for (int u2 = 0; u2 < W[2]; ++u2)
                             for (int u1 = 0; u1 < W[1]; ++u1)
                                 for (int u0 = 0; u0 < W[0]; ++u0) {
@@ -537,11 +534,11 @@ __global__ void k_galerkin(const PatchDesc* pd, const int* plist, int depth, dou
                                         mul *= 2 * P.p[r] + 1;
                                     }
                                     if (!ok2 || pb == 0.0) continue;
-                                    acc += pa * pb * K64[F.koff + (long long)sa * F.Sp + of];
+                                    acc += pa * pb * K64[F.koff + ieti_val_pos(F.m, P.p, F.S, a[0], a[1], a[2], of)];
                                 }
                     }
         }
-        K64[C.koff + (long long)s * C.Sp + O] = acc;
+        K64[C.koff + ieti_val_pos(C.m, P.p, C.S, Ii[0], Ii[1], Ii[2], O)] = acc;
     }
 }
 
@@ -619,8 +616,7 @@ __global__ void k_coarse_inverse(const PatchDesc* pd, const double* K64, const d
                 if (band && r < P.dim) mprod *= tab[L.mw[r] + ii[r] * (2 * P.p[r] + 1) + dl + P.p[r]];
             }
             if (band) {
-                int s = ieti_store_pos(L.m, P.p, ii[0], ii[1], ii[2]);
-                v = K64[L.koff + (long long)s * L.Sp + of] + al * mprod;
+                v = K64[L.koff + ieti_val_pos(L.m, P.p, L.S, ii[0], ii[1], ii[2], of)] + al * mprod;
             }
         }
         A[t] = v;
@@ -643,40 +639,21 @@ __global__ void k_regularize(const PatchDesc* pd, const double* K64, const doubl
     if (!P.floating) return;
     for (int l = 0; l < P.L; ++l) {
         const LevelDesc& L = P.lev[l];
-        long long total = (long long)L.n * L.Sp;
+        long long total = (long long)L.n * L.S;
         for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
              t += (long long)gridDim.x * blockDim.x) {
-            int s = (int)(t / L.Sp), o = (int)(t % L.Sp);
-            double v = K64[L.koff + t];
-            if (o < L.S) {
-                // natural row of storage position s
-                int ncol = ieti_ncolors(P.p), c = 0, off = 0;
-                int cc0 = 0, cc1 = 0, cc2 = 0, k0 = 1, k1 = 1;
-                for (c = 0; c < ncol; ++c) {
-                    int c0 = c % (P.p[0] + 1), c1 = (c / (P.p[0] + 1)) % (P.p[1] + 1), c2 = c / ((P.p[0] + 1) * (P.p[1] + 1));
-                    int o2 = ieti_color_off(L.m, P.p, c0, c1, c2);
-                    int cnt = ieti_cnt(L.m[0], P.p[0], c0) * ieti_cnt(L.m[1], P.p[1], c1) * ieti_cnt(L.m[2], P.p[2], c2);
-                    if (s >= o2 && s < o2 + cnt) {
-                        cc0 = c0; cc1 = c1; cc2 = c2; off = o2;
-                        k0 = ieti_cnt(L.m[0], P.p[0], c0);
-                        k1 = ieti_cnt(L.m[1], P.p[1], c1);
-                        break;
-                    }
-                }
-                int tt = s - off;
-                int i0 = cc0 + (P.p[0] + 1) * (tt % k0), i1 = cc1 + (P.p[1] + 1) * ((tt / k0) % k1),
-                    i2 = cc2 + (P.p[2] + 1) * (tt / (k0 * k1));
-                int ii[3] = {i0, i1, i2}, rem = o;
-                double mm = 1.0;
-                for (int r = 0; r < 3; ++r) {
-                    int w = 2 * P.p[r] + 1;
-                    int orr = rem % w;
-                    rem /= w;
-                    if (r < P.dim) mm *= tab[L.mw[r] + ii[r] * w + orr];
-                }
-                v += alpha * mm;
+            int i = (int)(t / L.S), o = (int)(t % L.S);
+            int ii[3] = {i % L.m[0], (i / L.m[0]) % L.m[1], i / (L.m[0] * L.m[1])};
+            long long pos = L.koff + ieti_val_pos(L.m, P.p, L.S, ii[0], ii[1], ii[2], o);
+            int rem = o;
+            double mm = 1.0;
+            for (int r = 0; r < 3; ++r) {
+                int w = 2 * P.p[r] + 1;
+                int orr = rem % w;
+                rem /= w;
+                if (r < P.dim) mm *= tab[L.mw[r] + ii[r] * w + orr];
             }
-            KM64[L.koff + t] = v;
+            KM64[pos] = K64[pos] + alpha * mm;
         }
     }
 }

@@ -22,6 +22,27 @@ namespace ieti_t {
 
 constexpr int kMaxRows = 64;
 
+// Optional self-check (compiled with -DIETI_DEBUG_BOUNDS): an index outside
+// its buffer is recorded in dbg[] (count, site, index, limit, block, thread)
+// and the access is skipped.
+#ifdef IETI_DEBUG_BOUNDS
+__device__ int* g_ieti_dbg;
+__device__ __forceinline__ bool ieti_ok(long long idx, long long lim, int site) {
+    if (idx >= 0 && idx < lim) return true;
+    if (g_ieti_dbg && atomicAdd(&g_ieti_dbg[0], 1) == 0) {
+        g_ieti_dbg[1] = site;
+        g_ieti_dbg[2] = (int)idx;
+        g_ieti_dbg[3] = (int)lim;
+        g_ieti_dbg[4] = blockIdx.x;
+        g_ieti_dbg[5] = threadIdx.x;
+    }
+    return false;
+}
+#define IETI_OK(idx, lim, site) ieti_ok((long long)(idx), (long long)(lim), (site))
+#else
+#define IETI_OK(idx, lim, site) true
+#endif
+
 struct Red {
     double v[32][4];
 };
@@ -86,10 +107,12 @@ __host__ __device__ inline Plan make_plan(const PatchDesc& P, size_t tsize, size
     if (pl.a0) used += ab;
     pl.mat_off = used;
     pl.ls = -1;
+    // levels 0..l are staged as one copy of their contiguous span in the
+    // value pool (including the alignment gaps between levels)
     for (int l = 0; l < P.L - 1; ++l) {
-        size_t mb = (size_t)P.lev[l].n * P.lev[l].Sp * tsize;
-        if (used + mb > B) break;
-        used += mb;
+        size_t span = (size_t)(P.lev[l].koff + (long long)P.lev[l].n * P.lev[l].S - P.lev[0].koff) * tsize;
+        if (pl.mat_off + span > B) break;
+        used = pl.mat_off + span;
         pl.ls = l;
     }
     pl.used = used;
@@ -99,7 +122,10 @@ __host__ __device__ inline Plan make_plan(const PatchDesc& P, size_t tsize, size
 // full shared-memory need of one slot (host side sizing)
 inline size_t smem_need(const PatchDesc& P, size_t tsize) {
     size_t b = ctab_bytes(P) + align16(vec_elems(P) * tsize) + align16((size_t)P.lev[0].n * P.lev[0].n * tsize);
-    for (int l = 0; l < P.L - 1; ++l) b += (size_t)P.lev[l].n * P.lev[l].Sp * tsize;
+    if (P.L > 1) {
+        const LevelDesc& Lt = P.lev[P.L - 2];
+        b += (size_t)(Lt.koff + (long long)Lt.n * Lt.S - P.lev[0].koff) * tsize;
+    }
     return b;
 }
 
@@ -162,34 +188,28 @@ struct VC {
         return t.xb + (i0 / C0 + 1) + t.xk0 * ((i1 / C1 + 1) + t.xk1 * (D == 3 ? i2 / C2 + 1 : 0));
     }
 
-    // one row of color CC at level l: returns (A x)_row, diagonal in *d
+    // one row of color CC at level l: returns (A x)_row, diagonal in *d.
+    // vb: the color's value block (offset-major), cnt its rows, q the row.
     template <int CC>
-    __device__ __forceinline__ T row(const T* __restrict__ vr, const T* x, int l, int t0, int t1, int t2,
-                                     T* d) const {
+    __device__ __forceinline__ T row(const T* __restrict__ vb, int cnt, int q, const T* x, int l, int t0, int t1,
+                                     int t2, T* d) const {
         constexpr int c0 = CC % C0, c1 = (CC / C0) % C1, c2 = CC / (C0 * C1);
         T acc[4] = {T(0), T(0), T(0), T(0)};
         const CTab* tl = ct + l * NC;
+        const T* vq = vb + q;
 #pragma unroll
-        for (int q = 0; q < SP / 4; ++q) {
-            T w[4];
-            load4<T>(vr + 4 * q, w);
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int o = 4 * q + j;
-                if (o < S) {
-                    const int o0 = o % W0 - P0, o1 = (o / W0) % W1 - P1, o2 = o / (W0 * W1) - P2;
-                    const int e0 = c0 + o0 + C0, e1 = c1 + o1 + C1, e2 = c2 + o2 + C2;
-                    const int n0 = e0 % C0, n1 = e1 % C1, n2 = e2 % C2;
-                    const int d0 = e0 / C0 - 1, d1 = e1 / C1 - 1, d2 = e2 / C2 - 1;
-                    const CTab& tn = tl[n0 + C0 * (n1 + C1 * n2)];
-                    const int pos = tn.xb + (t0 + d0 + 1) +
-                                    tn.xk0 * ((t1 + d1 + 1) + (D == 3 ? tn.xk1 * (t2 + d2 + 1) : 0));
-                    acc[j] += w[j] * x[pos];
-                }
-            }
+        for (int o = 0; o < S; ++o) {
+            const int o0 = o % W0 - P0, o1 = (o / W0) % W1 - P1, o2 = o / (W0 * W1) - P2;
+            const int e0 = c0 + o0 + C0, e1 = c1 + o1 + C1, e2 = c2 + o2 + C2;
+            const int n0 = e0 % C0, n1 = e1 % C1, n2 = e2 % C2;
+            const int d0 = e0 / C0 - 1, d1 = e1 / C1 - 1, d2 = e2 / C2 - 1;
+            const CTab& tn = tl[n0 + C0 * (n1 + C1 * n2)];
+            const int pos = tn.xb + (t0 + d0 + 1) + tn.xk0 * ((t1 + d1 + 1) + (D == 3 ? tn.xk1 * (t2 + d2 + 1) : 0));
+            if (IETI_OK(pos, P->lev[l].nx, 1) && IETI_OK(q + (long long)o * cnt, (long long)cnt * S, 2))
+                acc[o & 3] += vq[(long long)o * cnt] * x[pos];
         }
         constexpr int oc = P0 + W0 * (P1 + W1 * P2);
-        *d = vr[oc];
+        *d = vq[(long long)oc * cnt];
         return (acc[0] + acc[1]) + (acc[2] + acc[3]);
     }
 
@@ -198,7 +218,7 @@ struct VC {
         constexpr int c0 = CC % C0, c1 = (CC / C0) % C1, c2 = CC / (C0 * C1);
         const LevelDesc& L = P->lev[l];
         const CTab t = ct[l * NC + CC];
-        const T* v = vals(l) + (long long)t.off * SP;
+        const T* v = vals(l) + (long long)t.off * S;
         T* x = X(l);
         const T* b = B(l) + t.off;
         const int cnt = t.k0 * t.k1 * t.k2;
@@ -208,9 +228,9 @@ struct VC {
             const int i0 = c0 + C0 * t0, i1 = c1 + C1 * t1, i2 = c2 + C2 * t2;
             if (ieti_masked(mask, L.m, i0, i1, i2)) continue;
             T dg;
-            const T ax = row<CC>(v + (long long)q * SP, x, l, t0, t1, t2, &dg);
+            const T ax = row<CC>(v, cnt, q, x, l, t0, t1, t2, &dg);
             const int pos = t.xb + (t0 + 1) + t.xk0 * ((t1 + 1) + (D == 3 ? t.xk1 * (t2 + 1) : 0));
-            x[pos] += (b[q] - ax) / dg;
+            if (IETI_OK(pos, L.nx, 3) && IETI_OK(t.off + q, L.n, 4)) x[pos] += (b[q] - ax) / dg;
         }
         __syncthreads();
     }
@@ -220,7 +240,7 @@ struct VC {
         constexpr int c0 = CC % C0, c1 = (CC / C0) % C1, c2 = CC / (C0 * C1);
         const LevelDesc& L = P->lev[l];
         const CTab t = ct[l * NC + CC];
-        const T* v = vals(l) + (long long)t.off * SP;
+        const T* v = vals(l) + (long long)t.off * S;
         const T* x = X(l);
         const T* b = B(l) + t.off;
         const int cnt = t.k0 * t.k1 * t.k2;
@@ -229,12 +249,13 @@ struct VC {
             const int t1 = tr % t.k1, t2 = tr / t.k1;
             const int i0 = c0 + C0 * t0, i1 = c1 + C1 * t1, i2 = c2 + C2 * t2;
             const int i = i0 + L.m[0] * (i1 + L.m[1] * i2);
+            if (!IETI_OK(i, P->lev[P->L - 1].n, 5)) continue;
             if (ieti_masked(mask, L.m, i0, i1, i2)) {
                 rs[i] = T(0);
                 continue;
             }
             T dg;
-            rs[i] = b[q] - row<CC>(v + (long long)q * SP, x, l, t0, t1, t2, &dg);
+            rs[i] = b[q] - row<CC>(v, cnt, q, x, l, t0, t1, t2, &dg);
         }
     }
 
@@ -267,11 +288,13 @@ struct VC {
         T* xc = X(l - 1);
         const int nxc = l - 1 >= 1 ? Cl.nx : Cl.n;
         for (int t = threadIdx.x; t < nxc; t += blockDim.x) xc[t] = T(0);
+        if (!IETI_OK(P->lev[l - 1].xoff + nxc, P->nlx + 1, 6)) return;
         for (int I = threadIdx.x; I < Cl.n; I += blockDim.x) {
             const int I0 = I % Cl.m[0], Ir = I / Cl.m[0];
             const int I1 = Ir % Cl.m[1], I2 = Ir / Cl.m[1];
             const int pp[3] = {P0, P1, P2};
             const int dst = l - 1 >= 1 ? ieti_store_pos(Cl.m, pp, I0, I1, I2) : I;
+            if (!IETI_OK(dst, Cl.n, 7)) continue;
             if (ieti_masked(mask, Cl.m, I0, I1, I2)) {
                 bc[dst] = T(0);
                 continue;
@@ -341,12 +364,13 @@ struct VC {
                         const int q0 = a0 + u0;
                         if (q0 >= Cl.m[0]) continue;
                         const int src = cnat ? q0 + Cl.m[0] * (q1 + Cl.m[1] * q2) : cm_pos(l - 1, q0, q1, q2);
-                        s += w0[u0] * xc[src];
+                        if (IETI_OK(src, cnat ? Cl.n : Cl.nx, 8)) s += w0[u0] * xc[src];
                     }
                     acc += ww1 * s;
                 }
             }
-            x[cm_pos(l, i0, i1, i2)] += acc;
+            const int dp = cm_pos(l, i0, i1, i2);
+            if (IETI_OK(dp, F.nx, 9)) x[dp] += acc;
         }
         __syncthreads();
     }
@@ -419,57 +443,52 @@ struct VC {
     }
 };
 
-// FP64 fine-level SpMV row (rows of masked functions return 0)
-template <int D, int P0, int P1, int P2>
-__device__ __forceinline__ double k64_row(const PatchDesc& P, const double* __restrict__ K64, const double* x,
-                                          int i, int mask) {
-    constexpr int W0 = 2 * P0 + 1, W1 = 2 * P1 + 1;
-    const LevelDesc& L = P.lev[P.L - 1];
-    const int m0 = L.m[0], m1 = L.m[1], m2 = L.m[2];
-    const int i0 = i % m0, ir = i / m0;
-    const int i1 = ir % m1, i2 = ir / m1;
-    if (ieti_masked(mask, L.m, i0, i1, i2)) return 0.0;
-    const int pp[3] = {P0, P1, P2};
-    const int s = ieti_store_pos(L.m, pp, i0, i1, i2);
-    const double* v = K64 + L.koff + (long long)s * L.Sp;
-    double acc = 0.0;
-#pragma unroll
-    for (int o2 = -P2; o2 <= P2; ++o2) {
-        const bool v2 = (unsigned)(i2 + o2) < (unsigned)m2;
-#pragma unroll
-        for (int o1 = -P1; o1 <= P1; ++o1) {
-            const bool v1 = v2 && (unsigned)(i1 + o1) < (unsigned)m1;
-            const int xb = i + m0 * (o1 + m1 * o2);
-#pragma unroll
-            for (int o0 = -P0; o0 <= P0; ++o0) {
-                const bool vv = v1 && (unsigned)(i0 + o0) < (unsigned)m0;
-                const int o = (o0 + P0) + W0 * ((o1 + P1) + W1 * (o2 + P2));
-                acc += __ldg(v + o) * x[vv ? xb + o0 : i];
-            }
-        }
-    }
-    return acc;
-}
-
-// y = K x over the fine level, rows masked by `rowmask` set to 0, and, when
-// `sub` is given, y = sub - K x instead; rows listed by `only` (0 = all rows,
-// 1 = interface rows: boundary rows not on the Dirichlet boundary) or 0.
+// y = K x (FP64, fine level), rows masked by `rowmask` set to 0; with `sub`,
+// y = sub + scale K x; `only` = 1 keeps interface rows (boundary rows not on
+// the Dirichlet boundary) and zeroes the others.  Rows are visited color by
+// color so that each stencil diagonal is read with unit stride.
 template <int D, int P0, int P1, int P2>
 __device__ __noinline__ void spmv64(const PatchDesc& P, const double* __restrict__ K64, const double* x, double* y,
                                     int rowmask, const double* sub, double scale, int only) {
+    constexpr int W0 = 2 * P0 + 1, W1 = 2 * P1 + 1, W2 = 2 * P2 + 1, S = W0 * W1 * W2;
+    constexpr int C0 = P0 + 1, C1 = P1 + 1, C2 = P2 + 1, NC = C0 * C1 * C2;
     const LevelDesc& F = P.lev[P.L - 1];
-    for (int i = threadIdx.x; i < F.n; i += blockDim.x) {
-        double v = 0.0;
-        bool take = true;
-        if (only == 1) {
-            const int i0 = i % F.m[0], ir = i / F.m[0];
-            const int i1 = ir % F.m[1], i2 = ir / F.m[1];
-            take = ieti_on_boundary(F.m, D, i0, i1, i2) && !ieti_masked(P.dmask, F.m, i0, i1, i2);
+    const int m0 = F.m[0], m1 = F.m[1], m2 = F.m[2];
+    const int pp[3] = {P0, P1, P2};
+    int off = 0;
+    for (int c = 0; c < NC; ++c) {
+        const int c0 = c % C0, c1 = (c / C0) % C1, c2 = c / (C0 * C1);
+        const int k0 = ieti_cnt(m0, P0, c0), k1 = ieti_cnt(m1, P1, c1), k2 = ieti_cnt(m2, P2, c2);
+        const int cnt = k0 * k1 * k2;
+        const double* vb = K64 + F.koff + (long long)off * S;
+        for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+            const int t0 = q % k0, tr = q / k0;
+            const int t1 = tr % k1, t2 = tr / k1;
+            const int i0 = c0 + C0 * t0, i1 = c1 + C1 * t1, i2 = c2 + C2 * t2;
+            const int i = i0 + m0 * (i1 + m1 * i2);
+            bool take = !ieti_masked(rowmask, F.m, i0, i1, i2);
+            if (only == 1) take = take && ieti_on_boundary(F.m, D, i0, i1, i2) && !ieti_masked(P.dmask, F.m, i0, i1, i2);
+            double v = 0.0;
+            if (take) {
+                double acc[4] = {0.0, 0.0, 0.0, 0.0};
+                const double* vq = vb + q;
+#pragma unroll
+                for (int o = 0; o < S; ++o) {
+                    const int o0 = o % W0 - P0, o1 = (o / W0) % W1 - P1, o2 = o / (W0 * W1) - P2;
+                    const bool ok = (unsigned)(i0 + o0) < (unsigned)m0 && (unsigned)(i1 + o1) < (unsigned)m1 &&
+                                    (unsigned)(i2 + o2) < (unsigned)m2;
+                    const int xi = ok ? i + o0 + m0 * (o1 + m1 * o2) : i;
+                    if (IETI_OK(off * (long long)S + q + (long long)o * cnt, (long long)F.n * S, 10) && IETI_OK(xi, F.n, 11))
+                        acc[o & 3] += __ldg(vq + (long long)o * cnt) * x[xi];
+                }
+                v = scale * ((acc[0] + acc[1]) + (acc[2] + acc[3]));
+            }
+            if (sub) v = sub[i] + v;
+            y[i] = v;
         }
-        if (take) v = scale * k64_row<D, P0, P1, P2>(P, K64, x, i, rowmask);
-        if (sub) v = sub[i] + v;
-        y[i] = v;
+        off += cnt;
     }
+    (void)pp;
     __syncthreads();
 }
 
@@ -483,7 +502,8 @@ __device__ void vcycle_apply(const VC<T, D, P0, P1, P2>& vc, const double* rin, 
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const int i0 = i % F.m[0], ir = i / F.m[0];
         const int i1 = ir % F.m[1], i2 = ir / F.m[1];
-        b[L > 1 ? ieti_store_pos(F.m, pp, i0, i1, i2) : i] = (T)rin[i];
+        const int bi = L > 1 ? ieti_store_pos(F.m, pp, i0, i1, i2) : i;
+        if (IETI_OK(bi, n, 12)) b[bi] = (T)rin[i];
     }
     __syncthreads();
     vc.run(nu1, nu2);
@@ -491,7 +511,8 @@ __device__ void vcycle_apply(const VC<T, D, P0, P1, P2>& vc, const double* rin, 
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const int i0 = i % F.m[0], ir = i / F.m[0];
         const int i1 = ir % F.m[1], i2 = ir / F.m[1];
-        zout[i] = (double)x[L > 1 ? vc.cm_pos(L - 1, i0, i1, i2) : i];
+        const int xi = L > 1 ? vc.cm_pos(L - 1, i0, i1, i2) : i;
+        zout[i] = IETI_OK(xi, L > 1 ? F.nx : n, 13) ? (double)x[xi] : 0.0;
     }
     __syncthreads();
 }
@@ -542,6 +563,10 @@ __global__ void __launch_bounds__(512) k_solve_t(SolveArgs a) {
     __shared__ PatchDesc sP;
     extern __shared__ __align__(16) unsigned char dyn[];
     const SlotDesc sd = a.slots[blockIdx.x];
+#ifdef IETI_DEBUG_BOUNDS
+    if (threadIdx.x == 0) g_ieti_dbg = a.dbg;
+    __syncthreads();
+#endif
     {
         const int* src = (const int*)(a.pd + sd.patch);
         int* dst = (int*)&sP;
@@ -564,7 +589,9 @@ __global__ void __launch_bounds__(512) k_solve_t(SolveArgs a) {
     const bool reg = kind == 0 && P.floating;
     const T* Kv = a.mixed ? (const T*)(const void*)(reg ? a.KM32 : a.K32)
                           : (const T*)(const void*)(reg ? a.KM64 : a.K64);
-    VC<T, D, P0, P1, P2> vc;
+    __shared__ VC<T, D, P0, P1, P2> vc_s;
+    VC<T, D, P0, P1, P2>& vc = vc_s;
+    if (threadIdx.x == 0) {
     vc.P = &P;
     vc.mask = kind == 0 ? P.dmask : allsides;
     vc.Kg = Kv;
@@ -579,17 +606,21 @@ __global__ void __launch_bounds__(512) k_solve_t(SolveArgs a) {
     vc.Ks = (const T*)(dyn + pl.mat_off);
     vc.A0 = pl.a0 ? (const T*)(dyn + pl.a0_off) : A0g;
     vc.ct = (const CTab*)(dyn + pl.tab_off);
+    }
+    __syncthreads();
     vc.build_tables((CTab*)(dyn + pl.tab_off));
     if (pl.a0) {
         T* dst = (T*)(dyn + pl.a0_off);
         const int nn = P.lev[0].n * P.lev[0].n;
-        for (int t = threadIdx.x; t < nn; t += blockDim.x) dst[t] = A0g[t];
+        for (int t = threadIdx.x; t < nn; t += blockDim.x)
+            if (IETI_OK(pl.a0_off + (t + 1) * (long long)sizeof(T), a.smem_bytes + 1, 16)) dst[t] = A0g[t];
     }
     if (pl.ls >= 0) {
         T* dst = (T*)(dyn + pl.mat_off);
-        const long long cnt = P.lev[pl.ls].koff + (long long)P.lev[pl.ls].n * P.lev[pl.ls].Sp - vc.kbase;
+        const long long cnt = P.lev[pl.ls].koff + (long long)P.lev[pl.ls].n * P.lev[pl.ls].S - vc.kbase;
         const T* src = Kv + vc.kbase;
-        for (long long t = threadIdx.x; t < cnt; t += blockDim.x) dst[t] = src[t];
+        for (long long t = threadIdx.x; t < cnt; t += blockDim.x)
+            if (IETI_OK(pl.mat_off + (t + 1) * (long long)sizeof(T), a.smem_bytes + 1, 15)) dst[t] = src[t];
     }
     __syncthreads();
     long long vcount = 0;
@@ -651,7 +682,8 @@ __global__ void __launch_bounds__(512) k_solve_t(SolveArgs a) {
             x[i] = 0.0;
         }
         __syncthreads();
-        for (int e = a.crow_ptr[sd.row] + threadIdx.x; e < a.crow_ptr[sd.row + 1]; e += blockDim.x) z[a.c_idx[e]] = 1.0;
+        for (int e = a.crow_ptr[sd.row] + threadIdx.x; e < a.crow_ptr[sd.row + 1]; e += blockDim.x)
+            if (IETI_OK(a.c_idx[e], n, 14)) z[a.c_idx[e]] = 1.0;
         __syncthreads();
         for (int i = threadIdx.x; i < n; i += blockDim.x) phicol[i] = z[i];
         spmv64<D, P0, P1, P2>(P, a.K64, z, r, P.dmask, nullptr, -1.0, 0);

@@ -47,8 +47,10 @@ struct Tabs {
 
 // (A x)_i for one row: banded stiffness of a level plus, when alpha != 0,
 // alpha times the Kronecker parameter mass.  Returns the diagonal in *diag.
+// vals: the color block of the row's color (offset-major), cnt its rows,
+// s the row's number q inside the color
 template <typename V, typename X, typename A>
-__device__ __forceinline__ A row_apply(const V* __restrict__ vals, int sp, int s, const X* x,
+__device__ __forceinline__ A row_apply(const V* __restrict__ vals, int cnt, int s, const X* x,
                                        const int* m, const int* p, int i0, int i1, int i2,
                                        const V* mt0, const V* mt1, const V* mt2, A alpha, A* diag) {
     int lo0 = max(-p[0], -i0), hi0 = min(p[0], m[0] - 1 - i0);
@@ -66,14 +68,14 @@ __device__ __forceinline__ A row_apply(const V* __restrict__ vals, int sp, int s
                 if (mt2) m12 *= (A)mt2[i2 * (2 * p[2] + 1) + o2 + p[2]];
             }
             for (int o0 = lo0; o0 <= hi0; ++o0) {
-                A v = (A)vals[(long long)s * sp + ob + o0];
+                A v = (A)vals[(long long)(ob + o0) * cnt + s];
                 if (alpha != A(0)) v += alpha * (A)mt0[i0 * w0 + o0 + p[0]] * m12;
                 acc += v * (A)x[xb + o0];
             }
         }
     if (diag) {
         int oc = ((p[2]) * w1 + p[1]) * w0 + p[0];
-        A d = (A)vals[(long long)s * sp + oc];
+        A d = (A)vals[(long long)oc * cnt + s];
         if (alpha != A(0)) {
             A mm = (A)mt0[i0 * w0 + p[0]] * (A)mt1[i1 * w1 + p[1]];
             if (mt2) mm *= (A)mt2[i2 * (2 * p[2] + 1) + p[2]];
@@ -128,7 +130,7 @@ struct VCycle {
                 int i0 = c0 + nc0 * t0, i1 = c1 + nc1 * t1, i2 = c2 + (p[2] + 1) * t2;
                 if (ieti_masked(mask, L.m, i0, i1, i2)) continue;
                 T d;
-                T ax = row_apply<T, T, T>(vals, L.Sp, off + t, x, L.m, p, i0, i1, i2, m0, m1, m2, alpha, &d);
+                T ax = row_apply<T, T, T>(vals + (long long)off * L.S, cnt, t, x, L.m, p, i0, i1, i2, m0, m1, m2, alpha, &d);
                 int i = i0 + L.m[0] * (i1 + L.m[1] * i2);
                 x[i] += (b[i] - ax) / d;
             }
@@ -161,7 +163,7 @@ struct VCycle {
                     r[i] = 0;
                     continue;
                 }
-                T ax = row_apply<T, T, T>(vals, L.Sp, off + t, x, L.m, p, i0, i1, i2, m0, m1, m2, alpha,
+                T ax = row_apply<T, T, T>(vals + (long long)off * L.S, cnt, t, x, L.m, p, i0, i1, i2, m0, m1, m2, alpha,
                                           (T*)nullptr);
                 r[i] = b[i] - ax;
             }
@@ -296,8 +298,11 @@ struct VCycle {
 __device__ __forceinline__ double k64_row(const PatchDesc& P, const double* K64, const double* x, int i) {
     const LevelDesc& L = P.lev[P.L - 1];
     int i0 = i % L.m[0], i1 = (i / L.m[0]) % L.m[1], i2 = i / (L.m[0] * L.m[1]);
-    int s = ieti_store_pos(L.m, P.p, i0, i1, i2);
-    return row_apply<double, double, double>(K64 + L.koff, L.Sp, s, x, L.m, P.p, i0, i1, i2, nullptr, nullptr,
+    int c0 = i0 % (P.p[0] + 1), c1 = i1 % (P.p[1] + 1), c2 = i2 % (P.p[2] + 1);
+    int k0 = ieti_cnt(L.m[0], P.p[0], c0), k1 = ieti_cnt(L.m[1], P.p[1], c1), k2 = ieti_cnt(L.m[2], P.p[2], c2);
+    int q = i0 / (P.p[0] + 1) + k0 * (i1 / (P.p[1] + 1) + k1 * (i2 / (P.p[2] + 1)));
+    return row_apply<double, double, double>(K64 + L.koff + (long long)ieti_color_off(L.m, P.p, c0, c1, c2) * L.S,
+                                             k0 * k1 * k2, q, x, L.m, P.p, i0, i1, i2, nullptr, nullptr,
                                              nullptr, 0.0, (double*)nullptr);
 }
 
