@@ -240,6 +240,12 @@ int ietidp_apply_Ktilde_inv(ietidp_handle* h, const double* g, double* u);
 int ietidp_get_primal_basis(ietidp_handle* h, int patch, double* phi, int* ncols);
 int ietidp_get_spp(ietidp_handle* h, double* spp_host);
 
+/* Profiling: per-phase clock cycles of the first CTA of the local solver
+ * kernel since setup (64 counters: [4l+0..3] sweeps, residual, restriction,
+ * prolongation at level l; [48] coarsest solve; [49] FP64 SpMV).  Zeros
+ * unless the library was built with IETIDP_PHASE_TIMERS=1. */
+int ietidp_phase_timers(ietidp_handle* h, long long* out64);
+
 int ietidp_destroy(ietidp_handle* h);
 
 const char* ietidp_last_error(void);

@@ -27,8 +27,14 @@ def nvcc():
 
 def _flags():
     # IETIDP_DEBUG_BOUNDS=1 builds the self-checking variant of the local
-    # solver (every computed index is checked against its buffer)
-    return FLAGS + (["-DIETI_DEBUG_BOUNDS"] if os.environ.get("IETIDP_DEBUG_BOUNDS") == "1" else [])
+    # solver (every computed index is checked against its buffer);
+    # IETIDP_PHASE_TIMERS=1 adds per-phase clock counters
+    f = list(FLAGS)
+    if os.environ.get("IETIDP_DEBUG_BOUNDS") == "1":
+        f.append("-DIETI_DEBUG_BOUNDS")
+    if os.environ.get("IETIDP_PHASE_TIMERS") == "1":
+        f.append("-DIETI_PHASE_TIMERS")
+    return f
 
 
 def _compile(src):

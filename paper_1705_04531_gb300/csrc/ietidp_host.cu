@@ -162,6 +162,7 @@ struct ietidp_handle {
     int* its = nullptr;
     int* flags = nullptr;
     int* dbg = nullptr;       // self-check record of debug builds (6 ints)
+    long long* phase = nullptr;   // phase timers of profiling builds (64)
     long long* vst = nullptr;     // [0..4] Neumann-type stats, [8..12] basis stats
     // torn buffers
     double *gF = nullptr, *uF = nullptr, *vS = nullptr, *wS = nullptr, *gR = nullptr, *tmp = nullptr;
@@ -550,6 +551,7 @@ static int run_solve(ietidp_handle* h, int mode, const std::vector<SlotGroup>& g
     a.ncycles = h->opt.dirichlet_vcycles;
     a.vstats = vst;
     a.dbg = h->dbg;
+    a.phase = h->phase;
     bool timed = mode == MODE_NEUMANN && h->nev_used + 2 <= (int)h->ev.size();
     if (timed) cudaEventRecord(h->ev[h->nev_used], h->st);
     if (groups.size() == 1) {
@@ -900,6 +902,8 @@ extern "C" int ietidp_setup(const iga_problem* P, const ietidp_options* opt_in, 
     CKH(h->mem.alloc(&h->uloc, h->nrows));
     CKH(h->mem.alloc(&h->flags, 1));
     CKH(h->mem.alloc(&h->dbg, 8));
+    CKH(h->mem.alloc(&h->phase, 64));
+    CUH(cudaMemsetAsync(h->phase, 0, sizeof(long long) * 64, st));
     CUH(cudaMemsetAsync(h->dbg, 0, sizeof(int) * 8, st));
     CKH(h->mem.alloc(&h->vst, 16));
     CUH(cudaMemsetAsync(h->flags, 0, sizeof(int), st));
@@ -1351,6 +1355,16 @@ extern "C" int ietidp_info_get(const ietidp_handle* h, ietidp_info* info) {
 extern "C" int ietidp_patch_offsets(const ietidp_handle* h, long long* off) {
     if (!h || !off) return fail(IETIDP_E_INVALID_ARG, "null argument");
     for (int k = 0; k <= h->npatch; ++k) off[k] = h->prob->toff[k];
+    return IETIDP_OK;
+}
+
+// Per-phase clock cycles of CTA 0 of the local solver kernel, accumulated
+// since the handle was created (non-zero only in builds compiled with
+// IETIDP_PHASE_TIMERS=1).
+extern "C" int ietidp_phase_timers(ietidp_handle* h, long long* out64) {
+    if (!h || !out64) return fail(IETIDP_E_INVALID_ARG, "null argument");
+    CU(cudaStreamSynchronize(h->st));
+    CU(cudaMemcpy(out64, h->phase, sizeof(long long) * 64, cudaMemcpyDeviceToHost));
     return IETIDP_OK;
 }
 

@@ -109,6 +109,7 @@ struct SolveArgs {
     long long* vstats;         // [0] V-cycles, [1] V-cycle fine dofs (atomically added)
     size_t smem_bytes;         // dynamic shared memory of the launch (specialised kernels)
     int* dbg;                  // self-check record (debug builds only)
+    long long* phase;          // phase timers (profiling builds only)
 };
 
 // generic kernel (degrees known at run time only)

@@ -64,3 +64,4 @@ cudaError_t launch_solve_variant(const SolveArgs& a, int dim, int p0, int p1, in
 size_t solve_smem_need(const PatchDesc& P, int mixed) {
     return ieti_t::smem_need(P, mixed ? sizeof(float) : sizeof(double));
 }
+

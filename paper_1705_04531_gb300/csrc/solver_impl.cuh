@@ -43,6 +43,18 @@ __device__ __forceinline__ bool ieti_ok(long long idx, long long lim, int site) 
 #define IETI_OK(idx, lim, site) true
 #endif
 
+// Optional phase timers (compiled with -DIETI_PHASE_TIMERS): thread 0 of CTA 0
+// adds the clock cycles of each barrier-delimited phase to phase[]:
+// [4*l + 0..3] = sweeps, residual, restriction, prolongation at level l,
+// [48] coarsest solve, [49] FP64 SpMV, [50] V-cycle conversions.
+#ifdef IETI_PHASE_TIMERS
+#define IETI_T0() long long _t0 = (threadIdx.x == 0 && blockIdx.x == 0) ? clock64() : 0
+#define IETI_T1(k) do { if (threadIdx.x == 0 && blockIdx.x == 0 && phase) phase[k] += clock64() - _t0; } while (0)
+#else
+#define IETI_T0() do {} while (0)
+#define IETI_T1(k) do {} while (0)
+#endif
+
 struct Red {
     double v[32][4];
 };
@@ -174,6 +186,7 @@ struct VC {
     T* bs;                // b of all levels (level >= 1 storage order, level 0 natural)
     T* rs;                // fine-level residual (natural)
     const CTab* ct;       // [l * NC + c]
+    long long* phase;     // phase timers (profiling builds)
 
     __device__ __forceinline__ const T* vals(int l) const {
         return l <= ls ? Ks + (P->lev[l].koff - kbase) : Kg + P->lev[l].koff;
@@ -407,14 +420,38 @@ struct VC {
             __syncthreads();
         }
         for (int l = L - 1; l >= 1; --l) {
-            for (int s = 0; s < nu1; ++s) sweep(l, true);
-            residual(l);
-            restrict_to(l);
+            {
+                IETI_T0();
+                for (int s = 0; s < nu1; ++s) sweep(l, true);
+                IETI_T1(4 * l + 0);
+            }
+            {
+                IETI_T0();
+                residual(l);
+                IETI_T1(4 * l + 1);
+            }
+            {
+                IETI_T0();
+                restrict_to(l);
+                IETI_T1(4 * l + 2);
+            }
         }
-        coarsest();
+        {
+            IETI_T0();
+            coarsest();
+            IETI_T1(48);
+        }
         for (int l = 1; l <= L - 1; ++l) {
-            prolong_add(l);
-            for (int s = 0; s < nu2; ++s) sweep(l, false);
+            {
+                IETI_T0();
+                prolong_add(l);
+                IETI_T1(4 * l + 3);
+            }
+            {
+                IETI_T0();
+                for (int s = 0; s < nu2; ++s) sweep(l, false);
+                IETI_T1(4 * l + 0);
+            }
         }
     }
 
@@ -449,12 +486,14 @@ struct VC {
 // color so that each stencil diagonal is read with unit stride.
 template <int D, int P0, int P1, int P2>
 __device__ __noinline__ void spmv64(const PatchDesc& P, const double* __restrict__ K64, const double* x, double* y,
-                                    int rowmask, const double* sub, double scale, int only) {
+                                    int rowmask, const double* sub, double scale, int only,
+                                    long long* phase = nullptr) {
     constexpr int W0 = 2 * P0 + 1, W1 = 2 * P1 + 1, W2 = 2 * P2 + 1, S = W0 * W1 * W2;
     constexpr int C0 = P0 + 1, C1 = P1 + 1, C2 = P2 + 1, NC = C0 * C1 * C2;
     const LevelDesc& F = P.lev[P.L - 1];
     const int m0 = F.m[0], m1 = F.m[1], m2 = F.m[2];
     const int pp[3] = {P0, P1, P2};
+    IETI_T0();
     int off = 0;
     for (int c = 0; c < NC; ++c) {
         const int c0 = c % C0, c1 = (c / C0) % C1, c2 = c / (C0 * C1);
@@ -490,6 +529,7 @@ __device__ __noinline__ void spmv64(const PatchDesc& P, const double* __restrict
     }
     (void)pp;
     __syncthreads();
+    IETI_T1(49);
 }
 
 template <typename T, int D, int P0, int P1, int P2>
@@ -606,6 +646,7 @@ __global__ void __launch_bounds__(512) k_solve_t(SolveArgs a) {
     vc.Ks = (const T*)(dyn + pl.mat_off);
     vc.A0 = pl.a0 ? (const T*)(dyn + pl.a0_off) : A0g;
     vc.ct = (const CTab*)(dyn + pl.tab_off);
+    vc.phase = a.phase;
     }
     __syncthreads();
     vc.build_tables((CTab*)(dyn + pl.tab_off));
@@ -653,7 +694,7 @@ __global__ void __launch_bounds__(512) k_solve_t(SolveArgs a) {
         const double* bb = a.in + P.toff;
         double* xx = a.out + P.toff;
         for (int c = 0; c < a.ncycles; ++c) {
-            spmv64<D, P0, P1, P2>(P, a.K64, xx, r, P.dmask, bb, -1.0, 0);
+            spmv64<D, P0, P1, P2>(P, a.K64, xx, r, P.dmask, bb, -1.0, 0, a.phase);
             for (int i = threadIdx.x; i < n; i += blockDim.x) {
                 const int i0 = i % F.m[0], ir = i / F.m[0];
                 const int i1 = ir % F.m[1], i2 = ir / F.m[1];
@@ -742,7 +783,7 @@ __global__ void __launch_bounds__(512) k_solve_t(SolveArgs a) {
         }
         for (it = 1; it <= a.maxit; ++it) {
             double s[1] = {0.0};
-            spmv64<D, P0, P1, P2>(P, a.K64, p, q, P.dmask, nullptr, 1.0, 0);
+            spmv64<D, P0, P1, P2>(P, a.K64, p, q, P.dmask, nullptr, 1.0, 0, a.phase);
             if (basis) project_kerC(a, P, q, coef);
             for (int i = threadIdx.x; i < n; i += blockDim.x) s[0] += p[i] * q[i];
             cta_sum<1>(s, red);

@@ -99,6 +99,7 @@ _SIGS = {
     "ietidp_apply_Ktilde_inv": (C.c_int, [_vp, _vp, _vp]),
     "ietidp_get_primal_basis": (C.c_int, [_vp, C.c_int, _vp, C.POINTER(C.c_int)]),
     "ietidp_get_spp": (C.c_int, [_vp, _vp]),
+    "ietidp_phase_timers": (C.c_int, [_vp, _vp]),
     "ietidp_destroy": (C.c_int, [_vp]),
     "ietidp_last_error": (C.c_char_p, []),
 }
@@ -294,6 +295,11 @@ class Solver:
         """V-cycles whose scratch is the library's static device array (no
         allocation; see ietidp_vcycles_noalloc in the header)."""
         _check(_lib.ietidp_vcycles_noalloc(self.h, _ptr(b), _ptr(x), int(ncycles)))
+
+    def phase_timers(self):
+        out = np.zeros(64, dtype=np.int64)
+        _check(_lib.ietidp_phase_timers(self.h, out.ctypes.data_as(C.c_void_p)))
+        return out
 
     def apply_K(self, x, y):
         _check(_lib.ietidp_apply_K(self.h, _ptr(x), _ptr(y)))
