@@ -30,6 +30,8 @@ struct LevelDesc {
     int Sp;            // padded row length of the value arrays
     int xoff, boff;    // specialised solver: offsets of x (color-major, ghost padded) and b (storage order)
     int nx;            // size of the color-major padded x of this level
+    int xk[3];         // uniform padded block extents (ceil(m_r/(p_r+1)) + 2; 1 if unused)
+    int blk;           // xk0*xk1*xk2: size of one color block
     int refined[3];    // 1 if this level halves the elements of level l-1 along r
     long long koff;    // offset of this level's values in the value arrays
     int voff;          // offset of this level's vectors in a slot's level block
@@ -100,20 +102,20 @@ __host__ __device__ inline long long ieti_val_pos(const int* m, const int* p, in
     return (long long)ieti_color_off(m, p, c0, c1, c2) * S + (long long)o * (k0 * k1 * k2) + q;
 }
 
-// color-major, ghost-padded vector layout of the specialised solver: color c
-// owns a (k0+2) x (k1+2) [x (k2+2)] block (one ghost layer per side, d = 3
-// only in direction 2); blocks follow each other in color order.
+// color-major, ghost-padded vector layout of the specialised solver: every
+// color owns one block of uniform extents (ceil(m_r/(p_r+1)) + 2) per
+// direction (a ghost layer on each side; the third extent is 1 in 2D);
+// blocks follow each other in color order.  Entry (t0,t1,t2) of color c sits
+// at c*blk + (t0+1) + xk0*((t1+1) + xk1*(t2+1)) (t2+1 -> 0 in 2D).
+__host__ __device__ inline int ieti_xk(int m, int p) { return (m + p) / (p + 1) + 2; }
 __host__ __device__ inline int ieti_cm_block(const int* m, const int* p, int dim, int c0, int c1, int c2) {
     int b = (ieti_cnt(m[0], p[0], c0) + 2) * (ieti_cnt(m[1], p[1], c1) + 2);
     if (dim == 3) b *= ieti_cnt(m[2], p[2], c2) + 2;
     return b;
 }
 __host__ __device__ inline int ieti_cm_size(const int* m, const int* p, int dim) {
-    int s = 0;
-    for (int c2 = 0; c2 < (dim == 3 ? p[2] + 1 : 1); ++c2)
-        for (int c1 = 0; c1 < p[1] + 1; ++c1)
-            for (int c0 = 0; c0 < p[0] + 1; ++c0) s += ieti_cm_block(m, p, dim, c0, c1, c2);
-    return s;
+    int blk = ieti_xk(m[0], p[0]) * ieti_xk(m[1], p[1]) * (dim == 3 ? ieti_xk(m[2], p[2]) : 1);
+    return blk * ieti_ncolors(p);
 }
 
 __host__ __device__ inline bool ieti_masked(int mask, const int* m, int i0, int i1, int i2) {

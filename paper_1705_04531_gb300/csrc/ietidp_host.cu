@@ -114,6 +114,7 @@ struct iga_problem {
 
 struct SlotGroup {        // slots served by one kernel specialisation
     int dim, p0, p1, p2;
+    bool generic = false;     // run-time-degree kernel (no specialisation, or vectors too large)
     SlotDesc* d = nullptr;
     int n = 0;
     int its_off = 0;
@@ -510,7 +511,7 @@ static int launch_group(ietidp_handle* h, SolveArgs a, const SlotGroup& g, cudaS
     a.its = h->its + g.its_off;
     a.smem_bytes = g.smem;
     cudaError_t e;
-    if (solve_variant_exists(g.dim, g.p0, g.p1, g.p2, a.mixed)) e = launch_solve_variant(a, g.dim, g.p0, g.p1, g.p2, 512, st);
+    if (!g.generic) e = launch_solve_variant(a, g.dim, g.p0, g.p1, g.p2, 512, st);
     else e = launch_solve(a, 512, st);
     h->launches += 1;
     if (e != cudaSuccess) return fail(IETIDP_E_CUDA, std::string("solve kernel: ") + cudaGetErrorString(e));
@@ -579,15 +580,20 @@ static int run_solve(ietidp_handle* h, int mode, const std::vector<SlotGroup>& g
 static int make_groups(ietidp_handle* h, const std::vector<SlotDesc>& slots, std::vector<SlotGroup>& out,
                        cudaStream_t st) {
     bool mixed = h->opt.precision == IETIDP_PREC_MIXED;
-    std::map<std::tuple<int, int, int, int>, std::vector<SlotDesc>> by;
+    // key: (dim, p0, p1, p2, generic) -- patches whose V-cycle vectors do not
+    // fit the shared-memory budget of the specialised kernel use the generic one
+    std::map<std::tuple<int, int, int, int, int>, std::vector<SlotDesc>> by;
     for (const SlotDesc& sd : slots) {
         const PatchDesc& P = h->pd[sd.patch];
-        by[std::make_tuple(P.dim, P.p[0], P.p[1], P.p[2])].push_back(sd);
+        int gen = !solve_variant_exists(P.dim, P.p[0], P.p[1], P.p[2], mixed) || solve_smem_min(P, mixed) > kSmemCap;
+        by[std::make_tuple(P.dim, P.p[0], P.p[1], P.p[2], gen)].push_back(sd);
     }
     int off = 0;
     for (auto& kv : by) {
         SlotGroup g;
-        std::tie(g.dim, g.p0, g.p1, g.p2) = kv.first;
+        int gen;
+        std::tie(g.dim, g.p0, g.p1, g.p2, gen) = kv.first;
+        g.generic = gen != 0;
         g.n = (int)kv.second.size();
         g.its_off = off;
         off += g.n;
@@ -826,6 +832,8 @@ extern "C" int ietidp_setup(const iga_problem* P, const ietidp_options* opt_in, 
             koff += (long long)L.n * L.Sp;
             L.voff = voff;
             voff += L.n;
+            for (int r = 0; r < 3; ++r) L.xk[r] = (r < d) ? ieti_xk(L.m[r], q.p[r]) : 1;
+            L.blk = L.xk[0] * L.xk[1] * L.xk[2];
             L.nx = l >= 1 ? ieti_cm_size(L.m, q.p, d) : L.n;
             L.xoff = xoff;
             xoff += (L.nx + 3) & ~3;

@@ -120,6 +120,8 @@ cudaError_t launch_solve_variant(const SolveArgs& a, int dim, int p0, int p1, in
                                  cudaStream_t st);
 // shared memory a specialised launch would use for this patch (uncapped)
 size_t solve_smem_need(const PatchDesc& P, int mixed);
+// shared memory below which the specialised kernel cannot run this patch
+size_t solve_smem_min(const PatchDesc& P, int mixed);
 
 // ---- dual / primal helpers ---------------------------------------------------
 struct DualArgs {

@@ -61,6 +61,10 @@ cudaError_t launch_solve_variant(const SolveArgs& a, int dim, int p0, int p1, in
     return dispatch_double(a, dim, p0, p1, p2, threads, st);
 }
 
+size_t solve_smem_min(const PatchDesc& P, int mixed) {
+    return ieti_t::smem_min(P, mixed ? sizeof(float) : sizeof(double));
+}
+
 size_t solve_smem_need(const PatchDesc& P, int mixed) {
     return ieti_t::smem_need(P, mixed ? sizeof(float) : sizeof(double));
 }

@@ -111,7 +111,7 @@ __host__ __device__ inline Plan make_plan(const PatchDesc& P, size_t tsize, size
     used += ctab_bytes(P);
     pl.vec_off = used;
     size_t vb = align16(vec_elems(P) * tsize);
-    pl.vec = used + vb <= B;
+    pl.vec = used + vb <= B;   // required by the specialised kernel (host checks)
     if (pl.vec) used += vb;
     size_t ab = align16((size_t)P.lev[0].n * P.lev[0].n * tsize);
     pl.a0 = used + ab <= B;
@@ -130,6 +130,9 @@ __host__ __device__ inline Plan make_plan(const PatchDesc& P, size_t tsize, size
     pl.used = used;
     return pl;
 }
+
+// shared memory the specialised kernel cannot do without (tables + vectors)
+inline size_t smem_min(const PatchDesc& P, size_t tsize) { return ctab_bytes(P) + align16(vec_elems(P) * tsize); }
 
 // full shared-memory need of one slot (host side sizing)
 inline size_t smem_need(const PatchDesc& P, size_t tsize) {
@@ -166,148 +169,153 @@ __device__ __forceinline__ void load4<double>(const double* p, double* w) {
     w[0] = a.x; w[1] = a.y; w[2] = b.x; w[3] = b.y;
 }
 
+// dynamic shared memory of the specialised kernel; arrays resident there are
+// addressed from this symbol so that the compiler emits shared-memory loads
+extern __shared__ __align__(16) unsigned char ieti_dyn[];
+
+template <typename T>
+__device__ __forceinline__ T* shm(int elem_off) {
+    return reinterpret_cast<T*>(ieti_dyn) + elem_off;
+}
+
 template <typename T, int D, int P0, int P1, int P2>
 struct VC {
     static constexpr int W0 = 2 * P0 + 1, W1 = 2 * P1 + 1, W2 = 2 * P2 + 1;
-    static constexpr int S = W0 * W1 * W2, SP = sp_of(S);
+    static constexpr int S = W0 * W1 * W2;
     static constexpr int C0 = P0 + 1, C1 = P1 + 1, C2 = P2 + 1, NC = C0 * C1 * C2;
     static constexpr int R0 = P0 + 2, R1 = P1 + 2, R2 = D == 3 ? P2 + 2 : 1;
 
     const PatchDesc* P;   // shared copy
     int mask;
     const T* Kg;          // global value pool (K or K + alpha M^)
-    const T* Ks;          // shared matrices of levels 0..ls
+    int ks_off;           // staged matrices of levels 0..ls (element offset in dynamic shared memory)
     int ls;
     long long kbase;
     const T* tab;
     const int* itab;
-    const T* A0;
-    T* xs;                // x of all levels (level >= 1 color-major padded, level 0 natural)
-    T* bs;                // b of all levels (level >= 1 storage order, level 0 natural)
-    T* rs;                // fine-level residual (natural)
+    int a0_off;           // coarsest inverse in shared memory (element offset), or -1
+    const T* A0g;
+    int x_off, b_off, r_off;   // vectors in shared memory (element offsets)
     const CTab* ct;       // [l * NC + c]
     long long* phase;     // phase timers (profiling builds)
 
-    __device__ __forceinline__ const T* vals(int l) const {
-        return l <= ls ? Ks + (P->lev[l].koff - kbase) : Kg + P->lev[l].koff;
-    }
-    __device__ __forceinline__ T* X(int l) const { return xs + P->lev[l].xoff; }
-    __device__ __forceinline__ T* B(int l) const { return bs + P->lev[l].boff; }
-
-    // color-major position of natural (i0,i1,i2) at level l >= 1
-    __device__ __forceinline__ int cm_pos(int l, int i0, int i1, int i2) const {
-        const int c = (i0 % C0) + C0 * ((i1 % C1) + C1 * (i2 % C2));
-        const CTab& t = ct[l * NC + c];
-        return t.xb + (i0 / C0 + 1) + t.xk0 * ((i1 / C1 + 1) + t.xk1 * (D == 3 ? i2 / C2 + 1 : 0));
-    }
-
-    // one row of color CC at level l: returns (A x)_row, diagonal in *d.
-    // vb: the color's value block (offset-major), cnt its rows, q the row.
-    template <int CC>
-    __device__ __forceinline__ T row(const T* __restrict__ vb, int cnt, int q, const T* x, int l, int t0, int t1,
-                                     int t2, T* d) const {
+    // one row of color CC at level l.  X: the row's own entry in x; offsets
+    // of the neighbours are e0(o0) + e1(o1) + e2(o2) (uniform color blocks).
+    template <int CC, bool VSH>
+    __device__ __forceinline__ T row(const T* __restrict__ vg, int vs_off, int cnt, int q, const T* X, int blk,
+                                     int xk0, int xk01, T* d) const {
         constexpr int c0 = CC % C0, c1 = (CC / C0) % C1, c2 = CC / (C0 * C1);
+        int e0[W0], e1[W1], e2[W2];
+#pragma unroll
+        for (int o = -P0; o <= P0; ++o) {
+            const int e = c0 + o + C0;
+            e0[o + P0] = (e % C0 - c0) * blk + (e / C0 - 1);
+        }
+#pragma unroll
+        for (int o = -P1; o <= P1; ++o) {
+            const int e = c1 + o + C1;
+            e1[o + P1] = (e % C1 - c1) * C0 * blk + (e / C1 - 1) * xk0;
+        }
+#pragma unroll
+        for (int o = -P2; o <= P2; ++o) {
+            const int e = c2 + o + C2;
+            e2[o + P2] = D == 3 ? (e % C2 - c2) * C0 * C1 * blk + (e / C2 - 1) * xk01 : 0;
+        }
         T acc[4] = {T(0), T(0), T(0), T(0)};
-        const CTab* tl = ct + l * NC;
-        const T* vq = vb + q;
 #pragma unroll
         for (int o = 0; o < S; ++o) {
-            const int o0 = o % W0 - P0, o1 = (o / W0) % W1 - P1, o2 = o / (W0 * W1) - P2;
-            const int e0 = c0 + o0 + C0, e1 = c1 + o1 + C1, e2 = c2 + o2 + C2;
-            const int n0 = e0 % C0, n1 = e1 % C1, n2 = e2 % C2;
-            const int d0 = e0 / C0 - 1, d1 = e1 / C1 - 1, d2 = e2 / C2 - 1;
-            const CTab& tn = tl[n0 + C0 * (n1 + C1 * n2)];
-            const int pos = tn.xb + (t0 + d0 + 1) + tn.xk0 * ((t1 + d1 + 1) + (D == 3 ? tn.xk1 * (t2 + d2 + 1) : 0));
-            if (IETI_OK(pos, P->lev[l].nx, 1) && IETI_OK(q + (long long)o * cnt, (long long)cnt * S, 2))
-                acc[o & 3] += vq[(long long)o * cnt] * x[pos];
+            const int o0 = o % W0, o1 = (o / W0) % W1, o2 = o / (W0 * W1);
+            const T a = VSH ? shm<T>(vs_off)[q + o * cnt] : __ldg(vg + q + (long long)o * cnt);
+            acc[o & 3] += a * X[e0[o0] + e1[o1] + e2[o2]];
         }
         constexpr int oc = P0 + W0 * (P1 + W1 * P2);
-        *d = vq[(long long)oc * cnt];
+        *d = VSH ? shm<T>(vs_off)[q + oc * cnt] : __ldg(vg + q + (long long)oc * cnt);
         return (acc[0] + acc[1]) + (acc[2] + acc[3]);
     }
 
-    template <int CC>
-    __device__ void color_step(int l) const {
+    // sweep (WHAT = 0) or residual (WHAT = 1) over the rows of color CC
+    template <int CC, bool VSH, int WHAT>
+    __device__ void color_pass(int l) const {
         constexpr int c0 = CC % C0, c1 = (CC / C0) % C1, c2 = CC / (C0 * C1);
         const LevelDesc& L = P->lev[l];
         const CTab t = ct[l * NC + CC];
-        const T* v = vals(l) + (long long)t.off * S;
-        T* x = X(l);
-        const T* b = B(l) + t.off;
+        const int m0 = L.m[0], m1 = L.m[1];
+        const int blk = L.blk, xk0 = L.xk[0], xk01 = L.xk[0] * L.xk[1];
         const int cnt = t.k0 * t.k1 * t.k2;
+        const long long vrel = (long long)t.off * S;
+        const T* vg = Kg + L.koff + vrel;
+        const int vs = ks_off + (int)(L.koff - kbase + vrel);
+        T* xl = shm<T>(x_off + L.xoff + CC * blk);
+        const T* bl = shm<T>(b_off + L.boff + t.off);
         for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
             const int t0 = q % t.k0, tr = q / t.k0;
             const int t1 = tr % t.k1, t2 = tr / t.k1;
             const int i0 = c0 + C0 * t0, i1 = c1 + C1 * t1, i2 = c2 + C2 * t2;
-            if (ieti_masked(mask, L.m, i0, i1, i2)) continue;
-            T dg;
-            const T ax = row<CC>(v, cnt, q, x, l, t0, t1, t2, &dg);
-            const int pos = t.xb + (t0 + 1) + t.xk0 * ((t1 + 1) + (D == 3 ? t.xk1 * (t2 + 1) : 0));
-            if (IETI_OK(pos, L.nx, 3) && IETI_OK(t.off + q, L.n, 4)) x[pos] += (b[q] - ax) / dg;
-        }
-        __syncthreads();
-    }
-
-    template <int CC>
-    __device__ void resid_color(int l) const {
-        constexpr int c0 = CC % C0, c1 = (CC / C0) % C1, c2 = CC / (C0 * C1);
-        const LevelDesc& L = P->lev[l];
-        const CTab t = ct[l * NC + CC];
-        const T* v = vals(l) + (long long)t.off * S;
-        const T* x = X(l);
-        const T* b = B(l) + t.off;
-        const int cnt = t.k0 * t.k1 * t.k2;
-        for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
-            const int t0 = q % t.k0, tr = q / t.k0;
-            const int t1 = tr % t.k1, t2 = tr / t.k1;
-            const int i0 = c0 + C0 * t0, i1 = c1 + C1 * t1, i2 = c2 + C2 * t2;
-            const int i = i0 + L.m[0] * (i1 + L.m[1] * i2);
-            if (!IETI_OK(i, P->lev[P->L - 1].n, 5)) continue;
-            if (ieti_masked(mask, L.m, i0, i1, i2)) {
-                rs[i] = T(0);
-                continue;
-            }
-            T dg;
-            rs[i] = b[q] - row<CC>(v, cnt, q, x, l, t0, t1, t2, &dg);
-        }
-    }
-
-    template <int CC>
-    __device__ __forceinline__ void color_dispatch(int c, int l, int what) const {
-        if constexpr (CC < NC) {
-            if (c == CC) {
-                if (what == 0) color_step<CC>(l);
-                else resid_color<CC>(l);
+            const bool msk = ieti_masked(mask, L.m, i0, i1, i2);
+            const int own = (t0 + 1) + xk0 * (t1 + 1) + (D == 3 ? xk01 * (t2 + 1) : 0);
+            if (WHAT == 0) {
+                if (msk) continue;
+                T dg;
+                const T ax = row<CC, VSH>(vg, vs, cnt, q, xl + own, blk, xk0, xk01, &dg);
+                xl[own] += (bl[q] - ax) / dg;
             } else {
-                color_dispatch<CC + 1>(c, l, what);
+                const int i = i0 + m0 * (i1 + m1 * i2);
+                T rv = T(0);
+                if (!msk) {
+                    T dg;
+                    rv = bl[q] - row<CC, VSH>(vg, vs, cnt, q, xl + own, blk, xk0, xk01, &dg);
+                }
+                shm<T>(r_off)[i] = rv;
             }
+        }
+        if (WHAT == 0) __syncthreads();
+    }
+
+    template <int CC, bool VSH, int WHAT>
+    __device__ __forceinline__ void color_dispatch(int c, int l) const {
+        if constexpr (CC < NC) {
+            if (c == CC) color_pass<CC, VSH, WHAT>(l);
+            else color_dispatch<CC + 1, VSH, WHAT>(c, l);
         }
     }
 
     __device__ void sweep(int l, bool forward) const {
-        for (int cc = 0; cc < NC; ++cc) color_dispatch<0>(forward ? cc : NC - 1 - cc, l, 0);
+        if (l <= ls) {
+            for (int cc = 0; cc < NC; ++cc) color_dispatch<0, true, 0>(forward ? cc : NC - 1 - cc, l);
+        } else {
+            for (int cc = 0; cc < NC; ++cc) color_dispatch<0, false, 0>(forward ? cc : NC - 1 - cc, l);
+        }
     }
 
     __device__ void residual(int l) const {
-        for (int c = 0; c < NC; ++c) color_dispatch<0>(c, l, 1);
+        if (l <= ls) {
+            for (int c = 0; c < NC; ++c) color_dispatch<0, true, 1>(c, l);
+        } else {
+            for (int c = 0; c < NC; ++c) color_dispatch<0, false, 1>(c, l);
+        }
         __syncthreads();
+    }
+
+    // color-major position of natural (i0,i1,i2) at level l >= 1
+    __device__ __forceinline__ int cm_pos(const LevelDesc& L, int i0, int i1, int i2) const {
+        const int c = (i0 % C0) + C0 * ((i1 % C1) + C1 * (i2 % C2));
+        return c * L.blk + (i0 / C0 + 1) + L.xk[0] * ((i1 / C1 + 1) + (D == 3 ? L.xk[1] * (i2 / C2 + 1) : 0));
     }
 
     // b_{l-1} = P^T r_l (r natural), x_{l-1} = 0
     __device__ void restrict_to(int l) const {
         const LevelDesc& F = P->lev[l];
         const LevelDesc& Cl = P->lev[l - 1];
-        T* bc = B(l - 1);
-        T* xc = X(l - 1);
+        T* bc = shm<T>(b_off + Cl.boff);
+        T* xc = shm<T>(x_off + Cl.xoff);
+        const T* rs = shm<T>(r_off);
         const int nxc = l - 1 >= 1 ? Cl.nx : Cl.n;
         for (int t = threadIdx.x; t < nxc; t += blockDim.x) xc[t] = T(0);
-        if (!IETI_OK(P->lev[l - 1].xoff + nxc, P->nlx + 1, 6)) return;
+        const int pp[3] = {P0, P1, P2};
         for (int I = threadIdx.x; I < Cl.n; I += blockDim.x) {
             const int I0 = I % Cl.m[0], Ir = I / Cl.m[0];
             const int I1 = Ir % Cl.m[1], I2 = Ir / Cl.m[1];
-            const int pp[3] = {P0, P1, P2};
             const int dst = l - 1 >= 1 ? ieti_store_pos(Cl.m, pp, I0, I1, I2) : I;
-            if (!IETI_OK(dst, Cl.n, 7)) continue;
             if (ieti_masked(mask, Cl.m, I0, I1, I2)) {
                 bc[dst] = T(0);
                 continue;
@@ -328,13 +336,13 @@ struct VC {
                     const int f1 = a1 + u1;
                     const bool ok1 = ok2 && f1 < F.m[1];
                     const T ww1 = w1[u1] * ww2;
-                    const T* rr = rs + F.m[0] * ((ok1 ? f1 : 0) + F.m[1] * (ok1 ? f2 : 0));
+                    const int rb = F.m[0] * ((ok1 ? f1 : 0) + F.m[1] * (ok1 ? f2 : 0));
                     T s = 0;
 #pragma unroll
                     for (int u0 = 0; u0 < R0; ++u0) {
                         const int f0 = a0 + u0;
                         const bool ok = ok1 && f0 < F.m[0];
-                        s += w0[u0] * (ok ? rr[f0] : T(0));
+                        s += w0[u0] * (ok ? rs[rb + f0] : T(0));
                     }
                     acc += ww1 * s;
                 }
@@ -348,8 +356,8 @@ struct VC {
     __device__ void prolong_add(int l) const {
         const LevelDesc& F = P->lev[l];
         const LevelDesc& Cl = P->lev[l - 1];
-        const T* xc = X(l - 1);
-        T* x = X(l);
+        const T* xc = shm<T>(x_off + Cl.xoff);
+        T* x = shm<T>(x_off + F.xoff);
         const bool cnat = l - 1 == 0;
         for (int i = threadIdx.x; i < F.n; i += blockDim.x) {
             const int i0 = i % F.m[0], ir = i / F.m[0];
@@ -376,30 +384,38 @@ struct VC {
                     for (int u0 = 0; u0 < R0; ++u0) {
                         const int q0 = a0 + u0;
                         if (q0 >= Cl.m[0]) continue;
-                        const int src = cnat ? q0 + Cl.m[0] * (q1 + Cl.m[1] * q2) : cm_pos(l - 1, q0, q1, q2);
-                        if (IETI_OK(src, cnat ? Cl.n : Cl.nx, 8)) s += w0[u0] * xc[src];
+                        const int src = cnat ? q0 + Cl.m[0] * (q1 + Cl.m[1] * q2) : cm_pos(Cl, q0, q1, q2);
+                        s += w0[u0] * xc[src];
                     }
                     acc += ww1 * s;
                 }
             }
-            const int dp = cm_pos(l, i0, i1, i2);
-            if (IETI_OK(dp, F.nx, 9)) x[dp] += acc;
+            x[cm_pos(F, i0, i1, i2)] += acc;
         }
         __syncthreads();
     }
 
     __device__ void coarsest() const {
         const int n = P->lev[0].n;
-        const T* b = B(0);
-        T* x = X(0);
+        const T* b = shm<T>(b_off + P->lev[0].boff);
+        T* x = shm<T>(x_off + P->lev[0].xoff);
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
             T acc0 = 0, acc1 = 0;
             int j = 0;
-            for (; j + 1 < n; j += 2) {
-                acc0 += A0[(long long)j * n + i] * b[j];
-                acc1 += A0[(long long)(j + 1) * n + i] * b[j + 1];
+            if (a0_off >= 0) {
+                const T* A = shm<T>(a0_off);
+                for (; j + 1 < n; j += 2) {
+                    acc0 += A[j * n + i] * b[j];
+                    acc1 += A[(j + 1) * n + i] * b[j + 1];
+                }
+                if (j < n) acc0 += A[j * n + i] * b[j];
+            } else {
+                for (; j + 1 < n; j += 2) {
+                    acc0 += A0g[(long long)j * n + i] * b[j];
+                    acc1 += A0g[(long long)(j + 1) * n + i] * b[j + 1];
+                }
+                if (j < n) acc0 += A0g[(long long)j * n + i] * b[j];
             }
-            if (j < n) acc0 += A0[(long long)j * n + i] * b[j];
             x[i] = acc0 + acc1;
         }
         __syncthreads();
@@ -414,7 +430,7 @@ struct VC {
             return;
         }
         {
-            T* x = X(L - 1);
+            T* x = shm<T>(x_off + P->lev[L - 1].xoff);
             const int nx = P->lev[L - 1].nx;
             for (int i = threadIdx.x; i < nx; i += blockDim.x) x[i] = T(0);
             __syncthreads();
@@ -455,7 +471,7 @@ struct VC {
         }
     }
 
-    // fill the color tables of every level >= 1
+    // fill the color tables of every level
     __device__ void build_tables(CTab* tabs) const {
         const int pp[3] = {P0, P1, P2};
         for (int e = threadIdx.x; e < P->L * NC; e += blockDim.x) {
@@ -467,14 +483,9 @@ struct VC {
             t.k0 = ieti_cnt(L.m[0], P0, c0);
             t.k1 = ieti_cnt(L.m[1], P1, c1);
             t.k2 = ieti_cnt(L.m[2], P2, c2);
-            t.xk0 = t.k0 + 2;
-            t.xk1 = t.k1 + 2;
-            int xb = 0;
-            for (int cc = 0; cc < c; ++cc) {
-                const int e0 = cc % C0, e1 = (cc / C0) % C1, e2 = cc / (C0 * C1);
-                xb += ieti_cm_block(L.m, pp, D, e0, e1, e2);
-            }
-            t.xb = xb;
+            t.xk0 = L.xk[0];
+            t.xk1 = L.xk[1];
+            t.xb = c * L.blk;
             tabs[e] = t;
         }
     }
@@ -537,22 +548,20 @@ __device__ void vcycle_apply(const VC<T, D, P0, P1, P2>& vc, const double* rin, 
     const int L = vc.P->L;
     const LevelDesc& F = vc.P->lev[L - 1];
     const int n = F.n;
-    T* b = vc.B(L - 1);
+    T* b = shm<T>(vc.b_off + F.boff);
     const int pp[3] = {P0, P1, P2};
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const int i0 = i % F.m[0], ir = i / F.m[0];
         const int i1 = ir % F.m[1], i2 = ir / F.m[1];
-        const int bi = L > 1 ? ieti_store_pos(F.m, pp, i0, i1, i2) : i;
-        if (IETI_OK(bi, n, 12)) b[bi] = (T)rin[i];
+        b[L > 1 ? ieti_store_pos(F.m, pp, i0, i1, i2) : i] = (T)rin[i];
     }
     __syncthreads();
     vc.run(nu1, nu2);
-    const T* x = vc.X(L - 1);
+    const T* x = shm<T>(vc.x_off + F.xoff);
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const int i0 = i % F.m[0], ir = i / F.m[0];
         const int i1 = ir % F.m[1], i2 = ir / F.m[1];
-        const int xi = L > 1 ? vc.cm_pos(L - 1, i0, i1, i2) : i;
-        zout[i] = IETI_OK(xi, L > 1 ? F.nx : n, 13) ? (double)x[xi] : 0.0;
+        zout[i] = (double)x[L > 1 ? vc.cm_pos(F, i0, i1, i2) : i];
     }
     __syncthreads();
 }
@@ -601,7 +610,7 @@ __global__ void __launch_bounds__(512) k_solve_t(SolveArgs a) {
     __shared__ Red red;
     __shared__ double coef[kMaxRows];
     __shared__ PatchDesc sP;
-    extern __shared__ __align__(16) unsigned char dyn[];
+    unsigned char* dyn = ieti_dyn;
     const SlotDesc sd = a.slots[blockIdx.x];
 #ifdef IETI_DEBUG_BOUNDS
     if (threadIdx.x == 0) g_ieti_dbg = a.dbg;
@@ -632,36 +641,34 @@ __global__ void __launch_bounds__(512) k_solve_t(SolveArgs a) {
     __shared__ VC<T, D, P0, P1, P2> vc_s;
     VC<T, D, P0, P1, P2>& vc = vc_s;
     if (threadIdx.x == 0) {
-    vc.P = &P;
-    vc.mask = kind == 0 ? P.dmask : allsides;
-    vc.Kg = Kv;
-    vc.tab = a.mixed ? (const T*)(const void*)a.tabf : (const T*)(const void*)a.tab;
-    vc.itab = a.itab;
-    T* vbase = pl.vec ? (T*)(dyn + pl.vec_off) : (T*)a.lv + sd.lv;
-    vc.xs = vbase;
-    vc.bs = vbase + P.nlx;
-    vc.rs = vbase + P.nlx + P.nlb;
-    vc.kbase = P.lev[0].koff;
-    vc.ls = pl.ls;
-    vc.Ks = (const T*)(dyn + pl.mat_off);
-    vc.A0 = pl.a0 ? (const T*)(dyn + pl.a0_off) : A0g;
-    vc.ct = (const CTab*)(dyn + pl.tab_off);
-    vc.phase = a.phase;
+        vc.P = &P;
+        vc.mask = kind == 0 ? P.dmask : allsides;
+        vc.Kg = Kv;
+        vc.tab = a.mixed ? (const T*)(const void*)a.tabf : (const T*)(const void*)a.tab;
+        vc.itab = a.itab;
+        vc.x_off = (int)(pl.vec_off / sizeof(T));
+        vc.b_off = vc.x_off + P.nlx;
+        vc.r_off = vc.b_off + P.nlb;
+        vc.kbase = P.lev[0].koff;
+        vc.ls = pl.ls;
+        vc.ks_off = (int)(pl.mat_off / sizeof(T));
+        vc.a0_off = pl.a0 ? (int)(pl.a0_off / sizeof(T)) : -1;
+        vc.A0g = A0g;
+        vc.ct = (const CTab*)(dyn + pl.tab_off);
+        vc.phase = a.phase;
     }
     __syncthreads();
     vc.build_tables((CTab*)(dyn + pl.tab_off));
     if (pl.a0) {
         T* dst = (T*)(dyn + pl.a0_off);
         const int nn = P.lev[0].n * P.lev[0].n;
-        for (int t = threadIdx.x; t < nn; t += blockDim.x)
-            if (IETI_OK(pl.a0_off + (t + 1) * (long long)sizeof(T), a.smem_bytes + 1, 16)) dst[t] = A0g[t];
+        for (int t = threadIdx.x; t < nn; t += blockDim.x) dst[t] = A0g[t];
     }
     if (pl.ls >= 0) {
         T* dst = (T*)(dyn + pl.mat_off);
-        const long long cnt = P.lev[pl.ls].koff + (long long)P.lev[pl.ls].n * P.lev[pl.ls].S - vc.kbase;
-        const T* src = Kv + vc.kbase;
-        for (long long t = threadIdx.x; t < cnt; t += blockDim.x)
-            if (IETI_OK(pl.mat_off + (t + 1) * (long long)sizeof(T), a.smem_bytes + 1, 15)) dst[t] = src[t];
+        const long long cnt = P.lev[pl.ls].koff + (long long)P.lev[pl.ls].n * P.lev[pl.ls].S - P.lev[0].koff;
+        const T* src = Kv + P.lev[0].koff;
+        for (long long t = threadIdx.x; t < cnt; t += blockDim.x) dst[t] = src[t];
     }
     __syncthreads();
     long long vcount = 0;
