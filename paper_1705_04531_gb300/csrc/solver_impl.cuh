@@ -199,27 +199,28 @@ struct VC {
     const CTab* ct;       // [l * NC + c]
     long long* phase;     // phase timers (profiling builds)
 
-    // one row of color CC at level l.  X: the row's own entry in x; offsets
-    // of the neighbours are e0(o0) + e1(o1) + e2(o2) (uniform color blocks).
-    template <int CC, bool VSH>
-    __device__ __forceinline__ T row(const T* __restrict__ vg, int vs_off, int cnt, int q, const T* X, int blk,
-                                     int xk0, int xk01, T* d) const {
-        constexpr int c0 = CC % C0, c1 = (CC / C0) % C1, c2 = CC / (C0 * C1);
+    // one row of color (c0,c1,c2) at level l.  X: the row's own entry in x;
+    // the neighbour at stencil offset (o0,o1,o2) lies e0(o0)+e1(o1)+e2(o2)
+    // entries away (uniform color blocks): with d_r = floor((c_r+o_r)/C_r),
+    // e_r = (o_r - C_r d_r) * stride_r * blk + d_r * xstride_r.
+    template <bool VSH>
+    __device__ __forceinline__ T row(const T* __restrict__ vg, int vs_off, int cnt, int q, const T* X, int c0,
+                                     int c1, int c2, int blk, int xk0, int xk01, T* d) const {
         int e0[W0], e1[W1], e2[W2];
 #pragma unroll
         for (int o = -P0; o <= P0; ++o) {
-            const int e = c0 + o + C0;
-            e0[o + P0] = (e % C0 - c0) * blk + (e / C0 - 1);
+            const int dd = (c0 + o + C0) / C0 - 1;
+            e0[o + P0] = (o - C0 * dd) * blk + dd;
         }
 #pragma unroll
         for (int o = -P1; o <= P1; ++o) {
-            const int e = c1 + o + C1;
-            e1[o + P1] = (e % C1 - c1) * C0 * blk + (e / C1 - 1) * xk0;
+            const int dd = (c1 + o + C1) / C1 - 1;
+            e1[o + P1] = (o - C1 * dd) * C0 * blk + dd * xk0;
         }
 #pragma unroll
         for (int o = -P2; o <= P2; ++o) {
-            const int e = c2 + o + C2;
-            e2[o + P2] = D == 3 ? (e % C2 - c2) * C0 * C1 * blk + (e / C2 - 1) * xk01 : 0;
+            const int dd = (c2 + o + C2) / C2 - 1;
+            e2[o + P2] = D == 3 ? (o - C2 * dd) * C0 * C1 * blk + dd * xk01 : 0;
         }
         T acc[4] = {T(0), T(0), T(0), T(0)};
 #pragma unroll
@@ -233,19 +234,19 @@ struct VC {
         return (acc[0] + acc[1]) + (acc[2] + acc[3]);
     }
 
-    // sweep (WHAT = 0) or residual (WHAT = 1) over the rows of color CC
-    template <int CC, bool VSH, int WHAT>
-    __device__ void color_pass(int l) const {
-        constexpr int c0 = CC % C0, c1 = (CC / C0) % C1, c2 = CC / (C0 * C1);
+    // sweep (WHAT = 0) or residual (WHAT = 1) over the rows of color c
+    template <bool VSH, int WHAT>
+    __device__ void color_pass(int l, int c) const {
+        const int c0 = c % C0, c1 = (c / C0) % C1, c2 = c / (C0 * C1);
         const LevelDesc& L = P->lev[l];
-        const CTab t = ct[l * NC + CC];
+        const CTab t = ct[l * NC + c];
         const int m0 = L.m[0], m1 = L.m[1];
         const int blk = L.blk, xk0 = L.xk[0], xk01 = L.xk[0] * L.xk[1];
         const int cnt = t.k0 * t.k1 * t.k2;
         const long long vrel = (long long)t.off * S;
         const T* vg = Kg + L.koff + vrel;
         const int vs = ks_off + (int)(L.koff - kbase + vrel);
-        T* xl = shm<T>(x_off + L.xoff + CC * blk);
+        T* xl = shm<T>(x_off + L.xoff + c * blk);
         const T* bl = shm<T>(b_off + L.boff + t.off);
         for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
             const int t0 = q % t.k0, tr = q / t.k0;
@@ -256,14 +257,14 @@ struct VC {
             if (WHAT == 0) {
                 if (msk) continue;
                 T dg;
-                const T ax = row<CC, VSH>(vg, vs, cnt, q, xl + own, blk, xk0, xk01, &dg);
+                const T ax = row<VSH>(vg, vs, cnt, q, xl + own, c0, c1, c2, blk, xk0, xk01, &dg);
                 xl[own] += (bl[q] - ax) / dg;
             } else {
                 const int i = i0 + m0 * (i1 + m1 * i2);
                 T rv = T(0);
                 if (!msk) {
                     T dg;
-                    rv = bl[q] - row<CC, VSH>(vg, vs, cnt, q, xl + own, blk, xk0, xk01, &dg);
+                    rv = bl[q] - row<VSH>(vg, vs, cnt, q, xl + own, c0, c1, c2, blk, xk0, xk01, &dg);
                 }
                 shm<T>(r_off)[i] = rv;
             }
@@ -271,27 +272,19 @@ struct VC {
         if (WHAT == 0) __syncthreads();
     }
 
-    template <int CC, bool VSH, int WHAT>
-    __device__ __forceinline__ void color_dispatch(int c, int l) const {
-        if constexpr (CC < NC) {
-            if (c == CC) color_pass<CC, VSH, WHAT>(l);
-            else color_dispatch<CC + 1, VSH, WHAT>(c, l);
-        }
-    }
-
     __device__ void sweep(int l, bool forward) const {
         if (l <= ls) {
-            for (int cc = 0; cc < NC; ++cc) color_dispatch<0, true, 0>(forward ? cc : NC - 1 - cc, l);
+            for (int cc = 0; cc < NC; ++cc) color_pass<true, 0>(l, forward ? cc : NC - 1 - cc);
         } else {
-            for (int cc = 0; cc < NC; ++cc) color_dispatch<0, false, 0>(forward ? cc : NC - 1 - cc, l);
+            for (int cc = 0; cc < NC; ++cc) color_pass<false, 0>(l, forward ? cc : NC - 1 - cc);
         }
     }
 
     __device__ void residual(int l) const {
         if (l <= ls) {
-            for (int c = 0; c < NC; ++c) color_dispatch<0, true, 1>(c, l);
+            for (int c = 0; c < NC; ++c) color_pass<true, 1>(l, c);
         } else {
-            for (int c = 0; c < NC; ++c) color_dispatch<0, false, 1>(c, l);
+            for (int c = 0; c < NC; ++c) color_pass<false, 1>(l, c);
         }
         __syncthreads();
     }
