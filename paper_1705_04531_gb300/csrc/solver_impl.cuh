@@ -496,42 +496,50 @@ __device__ __noinline__ void spmv64(const PatchDesc& P, const double* __restrict
     constexpr int C0 = P0 + 1, C1 = P1 + 1, C2 = P2 + 1, NC = C0 * C1 * C2;
     const LevelDesc& F = P.lev[P.L - 1];
     const int m0 = F.m[0], m1 = F.m[1], m2 = F.m[2];
-    const int pp[3] = {P0, P1, P2};
     IETI_T0();
-    int off = 0;
-    for (int c = 0; c < NC; ++c) {
-        const int c0 = c % C0, c1 = (c / C0) % C1, c2 = c / (C0 * C1);
-        const int k0 = ieti_cnt(m0, P0, c0), k1 = ieti_cnt(m1, P1, c1), k2 = ieti_cnt(m2, P2, c2);
-        const int cnt = k0 * k1 * k2;
-        const double* vb = K64 + F.koff + (long long)off * S;
-        for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
-            const int t0 = q % k0, tr = q / k0;
-            const int t1 = tr % k1, t2 = tr / k1;
-            const int i0 = c0 + C0 * t0, i1 = c1 + C1 * t1, i2 = c2 + C2 * t2;
-            const int i = i0 + m0 * (i1 + m1 * i2);
-            bool take = !ieti_masked(rowmask, F.m, i0, i1, i2);
-            if (only == 1) take = take && ieti_on_boundary(F.m, D, i0, i1, i2) && !ieti_masked(P.dmask, F.m, i0, i1, i2);
-            double v = 0.0;
-            if (take) {
-                double acc[4] = {0.0, 0.0, 0.0, 0.0};
-                const double* vq = vb + q;
+    // all rows at once (no dependency between colors): row s of the storage
+    // order belongs to the color whose range [off, off + cnt) contains it
+    int kk0[C0], kk1[C1], kk2[C2];
 #pragma unroll
-                for (int o = 0; o < S; ++o) {
-                    const int o0 = o % W0 - P0, o1 = (o / W0) % W1 - P1, o2 = o / (W0 * W1) - P2;
-                    const bool ok = (unsigned)(i0 + o0) < (unsigned)m0 && (unsigned)(i1 + o1) < (unsigned)m1 &&
-                                    (unsigned)(i2 + o2) < (unsigned)m2;
-                    const int xi = ok ? i + o0 + m0 * (o1 + m1 * o2) : i;
-                    if (IETI_OK(off * (long long)S + q + (long long)o * cnt, (long long)F.n * S, 10) && IETI_OK(xi, F.n, 11))
-                        acc[o & 3] += __ldg(vq + (long long)o * cnt) * x[xi];
-                }
-                v = scale * ((acc[0] + acc[1]) + (acc[2] + acc[3]));
-            }
-            if (sub) v = sub[i] + v;
-            y[i] = v;
+    for (int c = 0; c < C0; ++c) kk0[c] = ieti_cnt(m0, P0, c);
+#pragma unroll
+    for (int c = 0; c < C1; ++c) kk1[c] = ieti_cnt(m1, P1, c);
+#pragma unroll
+    for (int c = 0; c < C2; ++c) kk2[c] = ieti_cnt(m2, P2, c);
+    for (int s = threadIdx.x; s < F.n; s += blockDim.x) {
+        int off = 0, c = 0, cnt = 0;
+#pragma unroll 1
+        for (c = 0; c < NC; ++c) {
+            cnt = kk0[c % C0] * kk1[(c / C0) % C1] * kk2[c / (C0 * C1)];
+            if (s < off + cnt) break;
+            off += cnt;
         }
-        off += cnt;
+        const int c0 = c % C0, c1 = (c / C0) % C1, c2 = c / (C0 * C1);
+        const int k0 = kk0[c0], k1 = kk1[c1];
+        const int q = s - off;
+        const int t0 = q % k0, tr = q / k0;
+        const int t1 = tr % k1, t2 = tr / k1;
+        const int i0 = c0 + C0 * t0, i1 = c1 + C1 * t1, i2 = c2 + C2 * t2;
+        const int i = i0 + m0 * (i1 + m1 * i2);
+        bool take = !ieti_masked(rowmask, F.m, i0, i1, i2);
+        if (only == 1) take = take && ieti_on_boundary(F.m, D, i0, i1, i2) && !ieti_masked(P.dmask, F.m, i0, i1, i2);
+        double v = 0.0;
+        if (take) {
+            double acc[4] = {0.0, 0.0, 0.0, 0.0};
+            const double* vq = K64 + F.koff + (long long)off * S + q;
+#pragma unroll
+            for (int o = 0; o < S; ++o) {
+                const int o0 = o % W0 - P0, o1 = (o / W0) % W1 - P1, o2 = o / (W0 * W1) - P2;
+                const bool ok = (unsigned)(i0 + o0) < (unsigned)m0 && (unsigned)(i1 + o1) < (unsigned)m1 &&
+                                (unsigned)(i2 + o2) < (unsigned)m2;
+                const int xi = ok ? i + o0 + m0 * (o1 + m1 * o2) : i;
+                acc[o & 3] += __ldg(vq + (long long)o * cnt) * x[xi];
+            }
+            v = scale * ((acc[0] + acc[1]) + (acc[2] + acc[3]));
+        }
+        if (sub) v = sub[i] + v;
+        y[i] = v;
     }
-    (void)pp;
     __syncthreads();
     IETI_T1(49);
 }
