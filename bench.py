@@ -48,8 +48,13 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--vcycle-reps", type=int, default=50)
-    ap.add_argument("--mode", default="bench", choices=["bench", "vcycle"],
-                    help="vcycle: setup plus three batched V-cycle launches (profiling target)")
+    ap.add_argument("--mode", default="bench", choices=["bench", "vcycle", "serve"],
+                    help="vcycle: setup plus three batched V-cycle launches (profiling target); "
+                         "serve: Poisson-arrival request stream through the continuous-batching server")
+    ap.add_argument("--rate", type=float, default=100.0, help="serve: arrivals per second")
+    ap.add_argument("--nreq", type=int, default=64, help="serve: requests in the stream")
+    ap.add_argument("--concurrency", type=int, default=8, help="serve: worker streams")
+    ap.add_argument("--budget-gb", type=float, default=64.0, help="serve: device memory budget")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     return ap.parse_args()
 
@@ -260,12 +265,55 @@ def run_vcycle_probe(args):
                       "x_norm": float(x.norm())}))
 
 
+def run_serve(args):
+    """Serving stream: m x m unit-square patch grids (m in {2,4,6,8}), p in
+    {2,3}, 16..128 elements per patch direction, f = 8 random sine modes,
+    Poisson arrivals at --rate; continuous batching with an HBM budget."""
+    import torch
+    from paper_1705_04531_gb300 import build
+    build.build()
+    from paper_1705_04531_gb300 import ietidp as api
+    stream = W.serving_stream(nreq=args.nreq, rate=args.rate, seed=0)
+    srv = api.Server(int(args.budget_gb * (1 << 30)), max_concurrent=args.concurrency,
+                     precision=args.precision)
+    # warm-up: one small request (module load, kernel attributes)
+    srv.wait(srv.submit(W.serving_stream(nreq=1, rate=1.0, seed=99, ms=(2,), ns=(16,))[0].domain))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tickets = []
+    for r in stream:
+        dt = t0 + r.arrival - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        tickets.append(srv.submit(r.domain))
+    lat, runs, its = [], [], []
+    for t in tickets:
+        state, u, st, tm = srv.wait(t)
+        lat.append(tm["latency_s"])
+        runs.append(tm["run_s"])
+        its.append(st["outer_it"])
+    t1 = time.perf_counter()
+    srv.close()
+    dofs = sum(sum(r.domain.patch_ndof(k) for k in range(r.domain.npatch)) for r in stream)
+    line = {"mode": "serve", "metric": "IETI-DP solves/sec (serving stream, each request assembled, set up and solved)",
+            "value": len(stream) / (t1 - t0), "unit": "solves/s", "n_gpus": 1,
+            "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+            "run_p50_ms": 1e3 * float(np.percentile(runs, 50)),
+            "config": {"workload": "serving stream (m in {2,4,6,8}, p in {2,3}, n in {16,32,64,128})",
+                       "requests": len(stream), "rate_per_s": args.rate, "concurrency": args.concurrency,
+                       "budget_gb": args.budget_gb, "precision": args.precision, "torn_dofs_total": dofs},
+            "outer_it_mean": float(np.mean(its)), "wall_s": t1 - t0}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.mode == "vcycle":
         return run_vcycle_probe(args)
+    if args.mode == "serve":
+        return run_serve(args)
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -248,6 +248,36 @@ int ietidp_phase_timers(ietidp_handle* h, long long* out64);
 
 int ietidp_destroy(ietidp_handle* h);
 
+/* ---- continuous-batching server ---------------------------------------
+ * Requests are queued as they arrive; a pool of `max_concurrent` worker
+ * threads, each with its own CUDA stream, admits queued requests while the
+ * estimated device memory of all admitted requests stays within
+ * `budget_bytes` (first come first served; a request that does not fit lets
+ * later smaller ones pass).  An admitted request runs iga_assemble_patches,
+ * ietidp_setup and the solve on its worker's stream, so the kernels of all
+ * admitted requests overlap on the device; its data stays resident until its
+ * solution is on the host.  The domain descriptor is copied at submission,
+ * except quad_values (device, must stay valid until the request is done).
+ * Each request's result is independent of what else runs (same kernels, same
+ * order of operations on its own buffers). */
+typedef struct ietidp_server ietidp_server;
+int ietidp_server_create(long long budget_bytes, int max_concurrent, const ietidp_options* opt,
+                         ietidp_server** out);
+/* IETIDP_E_BUDGET if the request alone exceeds the budget. */
+int ietidp_server_submit(ietidp_server* s, const iga_domain_desc* dom, unsigned long long* ticket);
+/* Poll (wait = 0) or wait for (wait = 1) a request; *state = 0 queued,
+ * 1 running, 2 done.  When done: u_host (n_u >= n_torn doubles, may be NULL)
+ * and stats are filled, t[3] (may be NULL) = queue time, run time and
+ * latency in seconds, the request's return code is returned, and the ticket
+ * is released. */
+int ietidp_server_poll(ietidp_server* s, unsigned long long ticket, int wait, int* state, double* u_host,
+                       long long n_u, ietidp_stats* stats, double* t);
+int ietidp_server_status(ietidp_server* s, int* running, long long* in_flight_bytes, int* queued);
+/* The admission estimate of a request's device memory (bytes), or -1. */
+long long ietidp_server_estimate(ietidp_server* s, const iga_domain_desc* dom);
+/* Finishes running requests, drops queued ones, joins the workers. */
+int ietidp_server_destroy(ietidp_server* s);
+
 const char* ietidp_last_error(void);
 
 #ifdef __cplusplus

@@ -45,7 +45,11 @@ int fail(int code, const std::string& msg) {
         if (rc_ != IETIDP_OK) return rc_; \
     } while (0)
 
+// Device allocations of one owner, stream-ordered (cudaMallocAsync /
+// cudaFreeAsync on the owner's stream), so that releasing one problem's memory
+// never synchronizes work that other streams have in flight.
 struct DevMem {
+    cudaStream_t st = nullptr;
     std::vector<void*> ptrs;
     long long bytes = 0;
     template <class T>
@@ -53,21 +57,24 @@ struct DevMem {
         *p = nullptr;
         if (n <= 0) n = 1;
         void* q = nullptr;
-        cudaError_t e = cudaMalloc(&q, sizeof(T) * (size_t)n);
-        if (e != cudaSuccess) return fail(IETIDP_E_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        cudaError_t e = cudaMallocAsync(&q, sizeof(T) * (size_t)n, st);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(IETIDP_E_OOM, std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
+        }
         ptrs.push_back(q);
         bytes += (long long)sizeof(T) * n;
         *p = (T*)q;
         return IETIDP_OK;
     }
     template <class T>
-    int upload(T** p, const std::vector<T>& v, cudaStream_t st) {
+    int upload(T** p, const std::vector<T>& v, cudaStream_t s) {
         CHK(alloc(p, (long long)v.size()));
-        if (!v.empty()) CU(cudaMemcpyAsync(*p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, st));
+        if (!v.empty()) CU(cudaMemcpyAsync(*p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, s));
         return IETIDP_OK;
     }
     void release() {
-        for (void* p : ptrs) cudaFree(p);
+        for (void* p : ptrs) cudaFreeAsync(p, st);
         ptrs.clear();
         bytes = 0;
     }
@@ -344,6 +351,7 @@ extern "C" int iga_assemble_patches(const iga_domain_desc* D, void* stream, iga_
         return fail(IETIDP_E_INVALID_ARG, "sin3d needs dim 3");
     auto* P = new iga_problem();
     P->stream = (cudaStream_t)stream;
+    P->mem.st = P->stream;
     int rc = build_topology(D, P);
     if (rc != IETIDP_OK) {
         delete P;
@@ -406,6 +414,7 @@ extern "C" int iga_assemble_patches(const iga_domain_desc* D, void* stream, iga_
     }
     long long total_qp = qpoff[N];
     DevMem scratch;
+    scratch.st = st;
     SetupArgs a{};
     a.npatch = N;
     a.dim = d;
@@ -482,6 +491,7 @@ extern "C" int iga_problem_load(const iga_problem* P, double* f_out) {
 extern "C" int iga_problem_free(iga_problem* P) {
     if (!P) return IETIDP_OK;
     P->mem.release();
+    cudaStreamSynchronize(P->stream);
     delete P;
     return IETIDP_OK;
 }
@@ -623,6 +633,7 @@ extern "C" int ietidp_setup(const iga_problem* P, const ietidp_options* opt_in, 
     h->prob = P;
     h->opt = opt;
     h->st = (cudaStream_t)stream;
+    h->mem.st = h->st;
     int rc = IETIDP_OK;
     auto bail = [&](int code) {
         h->mem.release();
@@ -955,6 +966,7 @@ extern "C" int ietidp_setup(const iga_problem* P, const ietidp_options* opt_in, 
     // ---- multigrid tables, Galerkin hierarchy, coarsest inverses -----------
     {
         DevMem scratch;
+        scratch.st = st;
         TableJob *d_tj = nullptr, *d_mj = nullptr;
         int* d_plist = nullptr;
         std::vector<int> plist(N);
@@ -1087,6 +1099,7 @@ extern "C" int ietidp_setup(const iga_problem* P, const ietidp_options* opt_in, 
     // ---- S_PiPi and its Cholesky factor -----------------------------------
     if (npi > 0) {
         DevMem scratch;
+        scratch.st = st;
         double *work, *sloc, *S, *cw;
         long long *d_soff;
         std::vector<long long> soff(N + 1, 0);
@@ -1433,6 +1446,7 @@ extern "C" int ietidp_destroy(ietidp_handle* h) {
     if (!h) return IETIDP_OK;
     cudaStreamSynchronize(h->st);
     h->mem.release();
+    cudaStreamSynchronize(h->st);
     if (h->h_pinned) cudaFreeHost(h->h_pinned);
     for (auto& ev : h->ev) cudaEventDestroy(ev);
     for (auto& sd : h->side) cudaStreamDestroy(sd);

@@ -102,6 +102,13 @@ _SIGS = {
     "ietidp_phase_timers": (C.c_int, [_vp, _vp]),
     "ietidp_destroy": (C.c_int, [_vp]),
     "ietidp_last_error": (C.c_char_p, []),
+    "ietidp_server_create": (C.c_int, [C.c_longlong, C.c_int, C.POINTER(ietidp_options), C.POINTER(_vp)]),
+    "ietidp_server_submit": (C.c_int, [_vp, C.POINTER(iga_domain_desc), C.POINTER(C.c_ulonglong)]),
+    "ietidp_server_poll": (C.c_int, [_vp, C.c_ulonglong, C.c_int, C.POINTER(C.c_int), _vp, C.c_longlong,
+                                     C.POINTER(ietidp_stats), _vp]),
+    "ietidp_server_status": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_longlong), C.POINTER(C.c_int)]),
+    "ietidp_server_estimate": (C.c_longlong, [_vp, C.POINTER(iga_domain_desc)]),
+    "ietidp_server_destroy": (C.c_int, [_vp]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -337,6 +344,67 @@ class Solver:
     def close(self):
         if self.h:
             _lib.ietidp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching server (ietidp_server_* in the C ABI).
+
+    ``submit`` returns a ticket; ``poll``/``wait`` return (state, u, stats,
+    times) -- u per patch layout on the host once the request is done."""
+
+    def __init__(self, budget_bytes, max_concurrent=4, **opts):
+        self.options = default_options(**opts)
+        self.h = C.c_void_p()
+        _check(_lib.ietidp_server_create(int(budget_bytes), int(max_concurrent), C.byref(self.options),
+                                         C.byref(self.h)))
+        self._keep = {}
+
+    def estimate(self, dom):
+        desc, keep = domain_desc(dom)
+        return int(_lib.ietidp_server_estimate(self.h, C.byref(desc)))
+
+    def submit(self, dom):
+        desc, keep = domain_desc(dom)
+        t = C.c_ulonglong()
+        _check(_lib.ietidp_server_submit(self.h, C.byref(desc), C.byref(t)))
+        n = int(sum(dom.patch_ndof(k) for k in range(dom.npatch)))
+        self._keep[t.value] = (keep, n)
+        return t.value
+
+    def poll(self, ticket, wait=False):
+        keep, n = self._keep[ticket]
+        state = C.c_int()
+        u = np.zeros(n)
+        st = ietidp_stats()
+        tm = np.zeros(3)
+        rc = _lib.ietidp_server_poll(self.h, C.c_ulonglong(ticket), int(wait), C.byref(state),
+                                     u.ctypes.data_as(C.c_void_p), n, C.byref(st),
+                                     tm.ctypes.data_as(C.c_void_p))
+        if state.value != 2:
+            _check(rc)
+            return state.value, None, None, None
+        del self._keep[ticket]
+        _check(rc)
+        return 2, u, st.as_dict(), {"queue_s": tm[0], "run_s": tm[1], "latency_s": tm[2]}
+
+    def wait(self, ticket):
+        return self.poll(ticket, wait=True)
+
+    def status(self):
+        r, b, q = C.c_int(), C.c_longlong(), C.c_int()
+        _check(_lib.ietidp_server_status(self.h, C.byref(r), C.byref(b), C.byref(q)))
+        return {"running": r.value, "in_flight_bytes": b.value, "queued": q.value}
+
+    def close(self):
+        if self.h:
+            _lib.ietidp_server_destroy(self.h)
             self.h = None
 
     def __del__(self):
