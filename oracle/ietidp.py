@@ -30,7 +30,9 @@ each row), local part of the jump operator B.
   relative residual tol_inner; then w = P z (Sec. 3.2: unconstrained solve
   followed by the energy-minimizing projection).  On patches without
   Dirichlet sides the right-hand side is first made exactly orthogonal to the
-  constants (the kernel of K), which it is in exact arithmetic.
+  constants (the kernel of K), which it is in exact arithmetic, and so is
+  every preconditioned residual (the CG iterates then differ only by
+  constants, which P removes).
 * F = B K~^{-1} B^T, d = B K~^{-1} f (Eq. 4); scaled Dirichlet preconditioner
   M_sD^{-1} = B_D S B_D^T with S = K_BB - K_BI K_II^{-1} K_IB; K_II^{-1} exact
   (D-D) or two V-cycles (MG-MG, Sec. 4).
@@ -344,8 +346,13 @@ class IETIDP:
             # accuracy of phi, so remove that component (exact in exact
             # arithmetic) to keep CG on the semidefinite K consistent.
             b -= b.mean()
+        # on floating patches the preconditioned residual is also made
+        # orthogonal to the constants: CG on the semidefinite K otherwise
+        # amplifies the rounding left in the constant mode by ~1/alpha
+        # (the iterates change only by constants, which P removes)
+        proj = (lambda z: z - z.mean()) if self.floating[k] else None
         z, it, ok = multigrid.pcg(lambda x: self.K[k] @ x, b, self.mgN[k].vcycle,
-                                  self.o.tol_inner, self.o.maxit_inner)
+                                  self.o.tol_inner, self.o.maxit_inner, project=proj)
         self.stats.neumann_its.append(it)
         return z - phi @ (C @ z) if npi else z
 

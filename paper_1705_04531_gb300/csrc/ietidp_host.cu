@@ -11,6 +11,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -128,7 +129,7 @@ struct SlotGroup {        // slots served by one kernel specialisation
     size_t smem = 0;
 };
 
-constexpr size_t kSmemCap = 220 * 1024;   // dynamic shared memory per CTA
+constexpr size_t kSmemCap = kSolveSmemCap;   // dynamic shared memory per CTA
 
 struct ietidp_handle {
     const iga_problem* prob = nullptr;
@@ -192,6 +193,10 @@ struct ietidp_handle {
 };
 
 extern "C" const char* ietidp_last_error(void) { return g_err.c_str(); }
+
+// set the calling thread's error text (used by the server to hand a worker's
+// error to the thread that polls the request)
+void ieti_set_error(const std::string& msg) { g_err = msg; }
 
 extern "C" void ietidp_default_options(ietidp_options* o) {
     std::memset(o, 0, sizeof(*o));
@@ -593,9 +598,14 @@ static int make_groups(ietidp_handle* h, const std::vector<SlotDesc>& slots, std
     // key: (dim, p0, p1, p2, generic) -- patches whose V-cycle vectors do not
     // fit the shared-memory budget of the specialised kernel use the generic one
     std::map<std::tuple<int, int, int, int, int>, std::vector<SlotDesc>> by;
+    // IETIDP_FORCE_GENERIC=1 routes every slot to the run-time-degree kernel
+    // (used to test that kernel on sizes the specialised one also handles)
+    const char* fg = std::getenv("IETIDP_FORCE_GENERIC");
+    const bool force_generic = fg && fg[0] == '1';
     for (const SlotDesc& sd : slots) {
         const PatchDesc& P = h->pd[sd.patch];
-        int gen = !solve_variant_exists(P.dim, P.p[0], P.p[1], P.p[2], mixed) || solve_smem_min(P, mixed) > kSmemCap;
+        int gen = force_generic || !solve_variant_exists(P.dim, P.p[0], P.p[1], P.p[2], mixed) ||
+                  solve_smem_min(P, mixed) > kSmemCap;
         by[std::make_tuple(P.dim, P.p[0], P.p[1], P.p[2], gen)].push_back(sd);
     }
     int off = 0;

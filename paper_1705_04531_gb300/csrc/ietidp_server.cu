@@ -26,6 +26,8 @@
 
 #include "../../include/ietidp.h"
 
+void ieti_set_error(const std::string& msg);   // ietidp_host.cu
+
 namespace {
 
 double now_s() {
@@ -246,6 +248,7 @@ extern "C" int ietidp_server_poll(ietidp_server* s, unsigned long long ticket, i
         t[2] = r->t_done - r->t_submit;
     }
     int rc = r->rc;
+    if (rc != IETIDP_OK) ieti_set_error("request " + std::to_string(ticket) + ": " + r->err);
     s->reqs.erase(it);
     return rc;
 }

@@ -63,6 +63,9 @@ cudaError_t launch_chol_linv(const double* A, int n, double* Linv, double* work,
                              cudaStream_t st);
 
 // ---- solve data --------------------------------------------------------------
+// dynamic shared memory budget of the specialised local solver kernel
+constexpr size_t kSolveSmemCap = 220 * 1024;
+
 struct SlotDesc {
     int patch;
     int kind;            // 0: Neumann hierarchy, 1: Dirichlet hierarchy

@@ -593,6 +593,16 @@ __device__ inline void project_kerC(const SolveArgs& a, const PatchDesc& P, doub
     __syncthreads();
 }
 
+// v <- v - mean(v) over the n entries (one CTA)
+__device__ inline void remove_mean(double* v, int n, Red& red) {
+    double s[1] = {0.0};
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s[0] += v[i];
+    cta_sum<1>(s, red);
+    const double mean = s[0] / n;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] -= mean;
+    __syncthreads();
+}
+
 __device__ inline void apply_C(const SolveArgs& a, const PatchDesc& P, const double* v, double* coef) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int j = w; j < P.npi; j += nw) {
@@ -775,10 +785,14 @@ __global__ void __launch_bounds__(512) k_solve_t(SolveArgs a) {
     int it = 0;
     bool conv = nb2 == 0.0;
     const double tol2 = a.tol * a.tol * nb2;
+    // floating patches (Neumann mode): keep the preconditioned residual
+    // orthogonal to the constants, the kernel of K
+    const bool proj1 = !basis && P.floating;
     if (!conv) {
         vcycle_apply(vc, r, z, a.nu1, a.nu2);
         ++vcount;
         if (basis) project_kerC(a, P, z, coef);
+        if (proj1) remove_mean(z, n, red);
         double rz;
         {
             double s[1] = {0.0};
@@ -816,6 +830,7 @@ __global__ void __launch_bounds__(512) k_solve_t(SolveArgs a) {
             vcycle_apply(vc, r, z, a.nu1, a.nu2);
             ++vcount;
             if (basis) project_kerC(a, P, z, coef);
+            if (proj1) remove_mean(z, n, red);
             double s3[2] = {0.0, 0.0};
             for (int i = threadIdx.x; i < n; i += blockDim.x) {
                 s3[0] += r[i] * z[i];
@@ -860,7 +875,10 @@ template <typename T, int D, int P0, int P1, int P2>
 cudaError_t launch_t(const SolveArgs& a, int threads, cudaStream_t st) {
     if (a.nslots == 0) return cudaSuccess;
     auto kern = k_solve_t<T, D, P0, P1, P2>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)a.smem_bytes);
+    // the attribute is an upper bound shared by all host threads: always set
+    // the fixed cap (a smaller value set by one thread could otherwise race
+    // with a larger launch from another)
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSolveSmemCap);
     if (e != cudaSuccess) return e;
     kern<<<a.nslots, threads, a.smem_bytes, st>>>(a);
     return cudaGetLastError();

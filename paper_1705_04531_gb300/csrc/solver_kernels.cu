@@ -354,6 +354,16 @@ __device__ void project_kerC(const SolveArgs& a, const PatchDesc& P, double* v, 
     __syncthreads();
 }
 
+// v <- v - mean(v) over the n entries (one CTA)
+__device__ void remove_mean(double* v, int n, Red& red) {
+    double s[1] = {0.0};
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s[0] += v[i];
+    cta_sum<1>(s, red);
+    const double mean = s[0] / n;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] -= mean;
+    __syncthreads();
+}
+
 // C rows of this patch applied to v: coef[j] = c_j . v
 __device__ void apply_C(const SolveArgs& a, const PatchDesc& P, const double* v, double* coef) {
     int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -511,10 +521,12 @@ __global__ void __launch_bounds__(512) k_solve(SolveArgs a) {
     int it = 0;
     bool conv = nb2 == 0.0;
     double tol2 = a.tol * a.tol * nb2;
+    const bool proj1 = !basis && P.floating;   // keep z orthogonal to the constants
     if (!conv) {
         vcycle_apply(vc, r, z, a.nu1, a.nu2);
         ++vcount;
         if (basis) project_kerC(a, P, z, coef);
+        if (proj1) remove_mean(z, n, red);
         double rz;
         {
             double s[1] = {0.0};
@@ -558,6 +570,7 @@ __global__ void __launch_bounds__(512) k_solve(SolveArgs a) {
                 vcycle_apply(vc, r, z, a.nu1, a.nu2);
                 ++vcount;
                 if (basis) project_kerC(a, P, z, coef);
+                if (proj1) remove_mean(z, n, red);
                 double s3[2] = {0.0, 0.0};
                 for (int i = threadIdx.x; i < n; i += blockDim.x) {
                     s3[0] += r[i] * z[i];

@@ -36,6 +36,16 @@ DOMS = {
                                        W.sine_modes_rhs(np.random.default_rng(5)), ("vertex", "edge")),
 }
 
+# run-time-degree kernel: degrees without a specialisation, and patches whose
+# V-cycle vectors exceed the shared-memory budget of the specialised kernel
+GENERIC = {
+    "square_p5": lambda: W.random_quad_rhs(W.uniform_grid(2, (2, 2), 5, 8, W.UNIT, None, ("vertex",)), seed=6),
+    "square_p3_n128": lambda: W.random_quad_rhs(W.uniform_grid(2, (2, 2), 3, 128, W.UNIT, None, ("vertex",)),
+                                                seed=8),
+    "grid3_p5_floating": lambda: W.random_quad_rhs(W.uniform_grid(2, (3, 3), 5, 8, W.UNIT, None,
+                                                                  ("vertex", "edge")), seed=9),
+}
+
 
 def relerr(got, ref):
     return np.sqrt(sum(np.sum((a - b) ** 2) for a, b in zip(got, ref)) / sum(np.sum(b ** 2) for b in ref))
@@ -112,6 +122,19 @@ def test_solve_matches_oracle(api, name, prec):
     unorm = np.sqrt(sum(np.sum(x ** 2) for x in got))
     jump = np.linalg.norm(orc.jump(got))
     assert jump <= 1e-9 * unorm
+
+
+@pytest.mark.parametrize("name", list(GENERIC))
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_generic_kernel_matches_oracle(api, name, prec):
+    dom = GENERIC[name]()
+    mp = Multipatch(dom)
+    ref = mp.to_patches(mp.solve_global())
+    prob = api.Problem(dom)
+    sol = api.Solver(prob, precision=prec)
+    u, st = sol.solve()
+    err = relerr(sol.split(u), ref)
+    assert st["converged"] and err <= 1e-8, (err, st)
 
 
 def test_symmetric_problem_skips_dual_cg(api):
