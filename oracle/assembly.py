@@ -115,3 +115,79 @@ def l2_error(dom, k, u_local, nq_extra=2):
     uh = Phi @ u_local
     ue = geometry.exact_solution(dom, X)
     return float(np.sum(w * np.abs(np.linalg.det(J)) * (uh - ue) ** 2))
+
+
+def row_stiffness_load(dom, k, i):
+    """Row i of patch k's stiffness and the load entry f_i, computed alone:
+    Gauss quadrature over the elements in the support of N_i only (same rule
+    as ``assemble_patch``).  Returns (column indices, values, f_i).  Used to
+    check single rows of a full-size solution one by one."""
+    d = dom.dim
+    deg = dom.patch_degree(k)
+    nel = dom.patch_nelem(k)
+    m = [n + p for n, p in zip(nel, deg)]
+    ii = []
+    rem = i
+    for r in range(d):
+        ii.append(rem % m[r])
+        rem //= m[r]
+    # per direction: elements of the support, their Gauss points, 1D tables
+    per = []
+    for r in range(d):
+        e_lo, e_hi = max(ii[r] - deg[r], 0), min(ii[r], nel[r] - 1)
+        g, w = np.polynomial.legendre.leggauss(deg[r] + 1)
+        xs, ws = [], []
+        for e in range(e_lo, e_hi + 1):
+            xs.append((e + 0.5 * (g + 1.0)) / nel[r])
+            ws.append(0.5 * w / nel[r])
+        x = np.concatenate(xs)
+        wq = np.concatenate(ws)
+        B, D = splines.basis_funs(splines.open_uniform_knots(nel[r], deg[r]), deg[r], x, deriv=True)
+        # global quadrature index (for Gauss-point right-hand sides)
+        qidx = np.concatenate([e * (deg[r] + 1) + np.arange(deg[r] + 1) for e in range(e_lo, e_hi + 1)])
+        per.append((x, wq, B, D, qidx))
+    mesh = np.meshgrid(*[p_[0] for p_ in per], indexing="ij")
+    xi = np.stack([mm.ravel() for mm in mesh], axis=1)
+    wm = np.meshgrid(*[p_[1] for p_ in per], indexing="ij")
+    w = np.ones(xi.shape[0])
+    for mm in wm:
+        w = w * mm.ravel()
+    X, J = geometry.patch_map(dom, k, xi)
+    detJ = np.linalg.det(J)
+    Jinv = np.linalg.inv(J)
+    G = np.einsum("qac,qbc->qab", Jinv, Jinv) * (w * np.abs(detJ))[:, None, None]
+    # values/gradients of all functions of the patch at these points (tensor)
+    nq = [len(p_[0]) for p_ in per]
+    idx = np.stack(np.meshgrid(*[np.arange(n) for n in nq], indexing="ij"), axis=-1).reshape(-1, d)
+    vals = np.ones((xi.shape[0], int(np.prod(m))))
+    grads = [np.ones_like(vals) for _ in range(d)]
+    for r in range(d):
+        Br = per[r][2][idx[:, r]]          # (q, m_r)
+        Dr = per[r][3][idx[:, r]]
+        # broadcast to the tensor grid of functions (first direction fastest)
+        full_B = np.ones((xi.shape[0],) + tuple(m[::-1]))
+        ax = d - r
+        bshape = [xi.shape[0]] + [1] * d
+        bshape[ax] = m[r]
+        vals = vals * np.broadcast_to(Br.reshape(bshape), full_B.shape).reshape(xi.shape[0], -1)
+        for a in range(d):
+            src = Dr if a == r else Br
+            grads[a] = grads[a] * np.broadcast_to(src.reshape(bshape), full_B.shape).reshape(xi.shape[0], -1)
+    gi = np.stack([g_[:, i] for g_ in grads], axis=1)          # (q, d)
+    row = np.zeros(int(np.prod(m)))
+    for a in range(d):
+        for b in range(d):
+            row += (G[:, a, b] * gi[:, a]) @ grads[b]
+    if dom.rhs["kind"] == "quad":
+        qs = dom.quad_shape(k)
+        flat = np.zeros(xi.shape[0], dtype=np.int64)
+        stride = 1
+        for r in range(d):
+            flat += per[r][4][idx[:, r]] * stride
+            stride *= qs[r]
+        fq = np.asarray(dom.rhs["values"][k])[flat]
+    else:
+        fq = geometry.rhs_values(dom, X)
+    f_i = float(np.sum(w * np.abs(detJ) * fq * vals[:, i]))
+    cols = np.nonzero(row)[0]
+    return cols, row[cols], f_i

@@ -122,7 +122,8 @@ struct iga_problem {
 
 struct SlotGroup {        // slots served by one kernel specialisation
     int dim, p0, p1, p2;
-    bool generic = false;     // run-time-degree kernel (no specialisation, or vectors too large)
+    bool generic = false;     // run-time-degree kernel (no specialisation)
+    bool xg = false;          // specialised kernel with V-cycle vectors in global memory
     SlotDesc* d = nullptr;
     int n = 0;
     int its_off = 0;
@@ -526,7 +527,7 @@ static int launch_group(ietidp_handle* h, SolveArgs a, const SlotGroup& g, cudaS
     a.its = h->its + g.its_off;
     a.smem_bytes = g.smem;
     cudaError_t e;
-    if (!g.generic) e = launch_solve_variant(a, g.dim, g.p0, g.p1, g.p2, 512, st);
+    if (!g.generic) e = launch_solve_variant(a, g.dim, g.p0, g.p1, g.p2, 512, st, g.xg);
     else e = launch_solve(a, 512, st);
     h->launches += 1;
     if (e != cudaSuccess) return fail(IETIDP_E_CUDA, std::string("solve kernel: ") + cudaGetErrorString(e));
@@ -595,8 +596,9 @@ static int run_solve(ietidp_handle* h, int mode, const std::vector<SlotGroup>& g
 static int make_groups(ietidp_handle* h, const std::vector<SlotDesc>& slots, std::vector<SlotGroup>& out,
                        cudaStream_t st) {
     bool mixed = h->opt.precision == IETIDP_PREC_MIXED;
-    // key: (dim, p0, p1, p2, generic) -- patches whose V-cycle vectors do not
-    // fit the shared-memory budget of the specialised kernel use the generic one
+    // key: (dim, p0, p1, p2, kind) with kind 0 = specialised, vectors in
+    // shared memory; 1 = specialised, vectors in global memory (they do not
+    // fit the budget); 2 = run-time-degree kernel (no specialisation)
     std::map<std::tuple<int, int, int, int, int>, std::vector<SlotDesc>> by;
     // IETIDP_FORCE_GENERIC=1 routes every slot to the run-time-degree kernel
     // (used to test that kernel on sizes the specialised one also handles)
@@ -604,8 +606,9 @@ static int make_groups(ietidp_handle* h, const std::vector<SlotDesc>& slots, std
     const bool force_generic = fg && fg[0] == '1';
     for (const SlotDesc& sd : slots) {
         const PatchDesc& P = h->pd[sd.patch];
-        int gen = force_generic || !solve_variant_exists(P.dim, P.p[0], P.p[1], P.p[2], mixed) ||
-                  solve_smem_min(P, mixed) > kSmemCap;
+        int gen = (force_generic || !solve_variant_exists(P.dim, P.p[0], P.p[1], P.p[2], mixed))
+                      ? 2
+                      : (solve_smem_min(P, mixed) > kSmemCap ? 1 : 0);
         by[std::make_tuple(P.dim, P.p[0], P.p[1], P.p[2], gen)].push_back(sd);
     }
     int off = 0;
@@ -613,12 +616,13 @@ static int make_groups(ietidp_handle* h, const std::vector<SlotDesc>& slots, std
         SlotGroup g;
         int gen;
         std::tie(g.dim, g.p0, g.p1, g.p2, gen) = kv.first;
-        g.generic = gen != 0;
+        g.generic = gen == 2;
+        g.xg = gen == 1;
         g.n = (int)kv.second.size();
         g.its_off = off;
         off += g.n;
         size_t need = 0;
-        for (const SlotDesc& sd : kv.second) need = std::max(need, solve_smem_need(h->pd[sd.patch], mixed));
+        for (const SlotDesc& sd : kv.second) need = std::max(need, solve_smem_need(h->pd[sd.patch], mixed, g.xg));
         g.smem = std::min(need, kSmemCap);
         CHK(h->mem.upload(&g.d, kv.second, st));
         out.push_back(g);

@@ -119,10 +119,12 @@ struct SolveArgs {
 cudaError_t launch_solve(const SolveArgs& a, int threads, cudaStream_t st);
 // kernel specialised for (dim, p0, p1, p2); cudaErrorNotSupported if none exists
 bool solve_variant_exists(int dim, int p0, int p1, int p2, int mixed);
+// xg: V-cycle vectors in global memory (patches whose vectors exceed the
+// shared-memory budget)
 cudaError_t launch_solve_variant(const SolveArgs& a, int dim, int p0, int p1, int p2, int threads,
-                                 cudaStream_t st);
+                                 cudaStream_t st, bool xg);
 // shared memory a specialised launch would use for this patch (uncapped)
-size_t solve_smem_need(const PatchDesc& P, int mixed);
+size_t solve_smem_need(const PatchDesc& P, int mixed, bool xg = false);
 // shared memory below which the specialised kernel cannot run this patch
 size_t solve_smem_min(const PatchDesc& P, int mixed);
 

@@ -104,14 +104,14 @@ __host__ __device__ inline size_t vec_elems(const PatchDesc& P) {
     return (size_t)P.nlx + P.nlb + P.lev[P.L - 1].n;
 }
 
-__host__ __device__ inline Plan make_plan(const PatchDesc& P, size_t tsize, size_t B) {
+__host__ __device__ inline Plan make_plan(const PatchDesc& P, size_t tsize, size_t B, bool want_vec) {
     Plan pl;
     size_t used = 0;
     pl.tab_off = 0;
     used += ctab_bytes(P);
     pl.vec_off = used;
     size_t vb = align16(vec_elems(P) * tsize);
-    pl.vec = used + vb <= B;   // required by the specialised kernel (host checks)
+    pl.vec = want_vec && used + vb <= B;   // vectors in shared memory (host checks they fit)
     if (pl.vec) used += vb;
     size_t ab = align16((size_t)P.lev[0].n * P.lev[0].n * tsize);
     pl.a0 = used + ab <= B;
@@ -134,9 +134,11 @@ __host__ __device__ inline Plan make_plan(const PatchDesc& P, size_t tsize, size
 // shared memory the specialised kernel cannot do without (tables + vectors)
 inline size_t smem_min(const PatchDesc& P, size_t tsize) { return ctab_bytes(P) + align16(vec_elems(P) * tsize); }
 
-// full shared-memory need of one slot (host side sizing)
-inline size_t smem_need(const PatchDesc& P, size_t tsize) {
-    size_t b = ctab_bytes(P) + align16(vec_elems(P) * tsize) + align16((size_t)P.lev[0].n * P.lev[0].n * tsize);
+// full shared-memory need of one slot (host side sizing); vectors included
+// unless they live in global memory (xg)
+inline size_t smem_need(const PatchDesc& P, size_t tsize, bool xg = false) {
+    size_t b = ctab_bytes(P) + (xg ? 0 : align16(vec_elems(P) * tsize)) +
+               align16((size_t)P.lev[0].n * P.lev[0].n * tsize);
     if (P.L > 1) {
         const LevelDesc& Lt = P.lev[P.L - 2];
         b += (size_t)(Lt.koff + (long long)Lt.n * Lt.S - P.lev[0].koff) * tsize;
@@ -178,7 +180,7 @@ __device__ __forceinline__ T* shm(int elem_off) {
     return reinterpret_cast<T*>(ieti_dyn) + elem_off;
 }
 
-template <typename T, int D, int P0, int P1, int P2>
+template <typename T, int D, int P0, int P1, int P2, bool XG>
 struct VC {
     static constexpr int W0 = 2 * P0 + 1, W1 = 2 * P1 + 1, W2 = 2 * P2 + 1;
     static constexpr int S = W0 * W1 * W2;
@@ -195,7 +197,13 @@ struct VC {
     const int* itab;
     int a0_off;           // coarsest inverse in shared memory (element offset), or -1
     const T* A0g;
-    int x_off, b_off, r_off;   // vectors in shared memory (element offsets)
+    int x_off, b_off, r_off;   // vectors: element offsets in shared memory, or in gvec when XG
+    T* gvec;              // the slot's level vectors in global memory (XG)
+
+    __device__ __forceinline__ T* vp(int off) const {
+        if constexpr (XG) return gvec + off;
+        else return shm<T>(off);
+    }
     const CTab* ct;       // [l * NC + c]
     long long* phase;     // phase timers (profiling builds)
 
@@ -246,8 +254,8 @@ struct VC {
         const long long vrel = (long long)t.off * S;
         const T* vg = Kg + L.koff + vrel;
         const int vs = ks_off + (int)(L.koff - kbase + vrel);
-        T* xl = shm<T>(x_off + L.xoff + c * blk);
-        const T* bl = shm<T>(b_off + L.boff + t.off);
+        T* xl = vp(x_off + L.xoff + c * blk);
+        const T* bl = vp(b_off + L.boff + t.off);
         for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
             const int t0 = q % t.k0, tr = q / t.k0;
             const int t1 = tr % t.k1, t2 = tr / t.k1;
@@ -266,7 +274,7 @@ struct VC {
                     T dg;
                     rv = bl[q] - row<VSH>(vg, vs, cnt, q, xl + own, c0, c1, c2, blk, xk0, xk01, &dg);
                 }
-                shm<T>(r_off)[i] = rv;
+                vp(r_off)[i] = rv;
             }
         }
         if (WHAT == 0) __syncthreads();
@@ -299,9 +307,9 @@ struct VC {
     __device__ void restrict_to(int l) const {
         const LevelDesc& F = P->lev[l];
         const LevelDesc& Cl = P->lev[l - 1];
-        T* bc = shm<T>(b_off + Cl.boff);
-        T* xc = shm<T>(x_off + Cl.xoff);
-        const T* rs = shm<T>(r_off);
+        T* bc = vp(b_off + Cl.boff);
+        T* xc = vp(x_off + Cl.xoff);
+        const T* rs = vp(r_off);
         const int nxc = l - 1 >= 1 ? Cl.nx : Cl.n;
         for (int t = threadIdx.x; t < nxc; t += blockDim.x) xc[t] = T(0);
         const int pp[3] = {P0, P1, P2};
@@ -349,8 +357,8 @@ struct VC {
     __device__ void prolong_add(int l) const {
         const LevelDesc& F = P->lev[l];
         const LevelDesc& Cl = P->lev[l - 1];
-        const T* xc = shm<T>(x_off + Cl.xoff);
-        T* x = shm<T>(x_off + F.xoff);
+        const T* xc = vp(x_off + Cl.xoff);
+        T* x = vp(x_off + F.xoff);
         const bool cnat = l - 1 == 0;
         for (int i = threadIdx.x; i < F.n; i += blockDim.x) {
             const int i0 = i % F.m[0], ir = i / F.m[0];
@@ -390,8 +398,8 @@ struct VC {
 
     __device__ void coarsest() const {
         const int n = P->lev[0].n;
-        const T* b = shm<T>(b_off + P->lev[0].boff);
-        T* x = shm<T>(x_off + P->lev[0].xoff);
+        const T* b = vp(b_off + P->lev[0].boff);
+        T* x = vp(x_off + P->lev[0].xoff);
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
             T acc0 = 0, acc1 = 0;
             int j = 0;
@@ -423,7 +431,7 @@ struct VC {
             return;
         }
         {
-            T* x = shm<T>(x_off + P->lev[L - 1].xoff);
+            T* x = vp(x_off + P->lev[L - 1].xoff);
             const int nx = P->lev[L - 1].nx;
             for (int i = threadIdx.x; i < nx; i += blockDim.x) x[i] = T(0);
             __syncthreads();
@@ -544,12 +552,12 @@ __device__ __noinline__ void spmv64(const PatchDesc& P, const double* __restrict
     IETI_T1(49);
 }
 
-template <typename T, int D, int P0, int P1, int P2>
-__device__ void vcycle_apply(const VC<T, D, P0, P1, P2>& vc, const double* rin, double* zout, int nu1, int nu2) {
+template <typename T, int D, int P0, int P1, int P2, bool XG>
+__device__ void vcycle_apply(const VC<T, D, P0, P1, P2, XG>& vc, const double* rin, double* zout, int nu1, int nu2) {
     const int L = vc.P->L;
     const LevelDesc& F = vc.P->lev[L - 1];
     const int n = F.n;
-    T* b = shm<T>(vc.b_off + F.boff);
+    T* b = vc.vp(vc.b_off + F.boff);
     const int pp[3] = {P0, P1, P2};
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const int i0 = i % F.m[0], ir = i / F.m[0];
@@ -558,7 +566,7 @@ __device__ void vcycle_apply(const VC<T, D, P0, P1, P2>& vc, const double* rin, 
     }
     __syncthreads();
     vc.run(nu1, nu2);
-    const T* x = shm<T>(vc.x_off + F.xoff);
+    const T* x = vc.vp(vc.x_off + F.xoff);
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const int i0 = i % F.m[0], ir = i / F.m[0];
         const int i1 = ir % F.m[1], i2 = ir / F.m[1];
@@ -616,7 +624,7 @@ __device__ inline void apply_C(const SolveArgs& a, const PatchDesc& P, const dou
     __syncthreads();
 }
 
-template <typename T, int D, int P0, int P1, int P2>
+template <typename T, int D, int P0, int P1, int P2, bool XG>
 __global__ void __launch_bounds__(512) k_solve_t(SolveArgs a) {
     __shared__ Red red;
     __shared__ double coef[kMaxRows];
@@ -645,19 +653,20 @@ __global__ void __launch_bounds__(512) k_solve_t(SolveArgs a) {
     const int kind = (a.mode == MODE_SCHUR) ? 1 : 0;
     const T* A0g = (a.mixed ? (const T*)(const void*)a.A0inv32 : (const T*)(const void*)a.A0inv64) + P.a0off[kind];
 
-    const Plan pl = make_plan(P, sizeof(T), a.smem_bytes);
+    const Plan pl = make_plan(P, sizeof(T), a.smem_bytes, !XG);
     const bool reg = kind == 0 && P.floating;
     const T* Kv = a.mixed ? (const T*)(const void*)(reg ? a.KM32 : a.K32)
                           : (const T*)(const void*)(reg ? a.KM64 : a.K64);
-    __shared__ VC<T, D, P0, P1, P2> vc_s;
-    VC<T, D, P0, P1, P2>& vc = vc_s;
+    __shared__ VC<T, D, P0, P1, P2, XG> vc_s;
+    VC<T, D, P0, P1, P2, XG>& vc = vc_s;
     if (threadIdx.x == 0) {
         vc.P = &P;
         vc.mask = kind == 0 ? P.dmask : allsides;
         vc.Kg = Kv;
         vc.tab = a.mixed ? (const T*)(const void*)a.tabf : (const T*)(const void*)a.tab;
         vc.itab = a.itab;
-        vc.x_off = (int)(pl.vec_off / sizeof(T));
+        vc.x_off = XG ? 0 : (int)(pl.vec_off / sizeof(T));
+        vc.gvec = (T*)a.lv + sd.lv;
         vc.b_off = vc.x_off + P.nlx;
         vc.r_off = vc.b_off + P.nlb;
         vc.kbase = P.lev[0].koff;
@@ -871,10 +880,10 @@ __global__ void __launch_bounds__(512) k_solve_t(SolveArgs a) {
     }
 }
 
-template <typename T, int D, int P0, int P1, int P2>
+template <typename T, int D, int P0, int P1, int P2, bool XG>
 cudaError_t launch_t(const SolveArgs& a, int threads, cudaStream_t st) {
     if (a.nslots == 0) return cudaSuccess;
-    auto kern = k_solve_t<T, D, P0, P1, P2>;
+    auto kern = k_solve_t<T, D, P0, P1, P2, XG>;
     // the attribute is an upper bound shared by all host threads: always set
     // the fixed cap (a smaller value set by one thread could otherwise race
     // with a larger launch from another)

@@ -1,0 +1,92 @@
+"""Full-size workloads on the GPU, in the configuration bench.py times.
+
+* quarter annulus 6x6, p=3, 64x64 elements per patch: the whole solution
+  against the oracle's conforming direct solve (rel. error <= 1e-8);
+* uneven 8x8 batch (degrees 2..4, 32..256 elements per direction) and the
+  2x2x2 cube (p=2, 32^3 elements per patch): too large for the oracle's
+  global solve, so sampled rows are checked one by one -- the oracle
+  computes single stiffness rows and load entries by quadrature, and the
+  GPU solution must satisfy K u = f on patch-interior rows -- and every
+  torn copy of an interface coefficient must agree (continuity, Eq. 2).
+"""
+import numpy as np
+import pytest
+
+from oracle import assembly
+from oracle.domain import Multipatch
+from paper_1705_04531_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1705_04531_gb300 import build
+    build.build()
+    from paper_1705_04531_gb300 import ietidp
+    return ietidp
+
+
+def _solve(api, dom, prec):
+    prob = api.Problem(dom)
+    sol = api.Solver(prob, precision=prec)
+    u, st = sol.solve()
+    out = sol.split(u)
+    sol.close()
+    prob.close()
+    return out, st
+
+
+def _jump(mp, u_patches):
+    hi = np.full(mp.nglob, -np.inf)
+    lo = np.full(mp.nglob, np.inf)
+    for k, u in enumerate(u_patches):
+        np.maximum.at(hi, mp.l2g[k], u)
+        np.minimum.at(lo, mp.l2g[k], u)
+    return float(np.max(hi - lo)), float(np.max(np.abs(hi)))
+
+
+def _interior_rows(dom, k, rng, count):
+    m = [n + p for n, p in zip(dom.patch_nelem(k), dom.patch_degree(k))]
+    rows = []
+    while len(rows) < count:
+        idx = [int(rng.integers(1, mr - 1)) for mr in m]
+        i = 0
+        stride = 1
+        for r, v in enumerate(idx):
+            i += v * stride
+            stride *= m[r]
+        rows.append(i)
+    return rows
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_annulus_full_size(api, prec):
+    dom = W.annulus_6x6(64, 3)
+    got, st = _solve(api, dom, prec)
+    mp = Multipatch(dom)
+    ref = mp.to_patches(mp.solve_global())
+    err = np.sqrt(sum(np.sum((a - b) ** 2) for a, b in zip(got, ref)) / sum(np.sum(b ** 2) for b in ref))
+    assert st["converged"] and err <= 1e-8, err
+
+
+@pytest.mark.parametrize("name", ["uneven8x8", "cube2x2x2"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_large_workloads_sampled(api, name, prec):
+    dom = W.uneven_8x8(0) if name == "uneven8x8" else W.cube_2x2x2(32, 2)
+    got, st = _solve(api, dom, prec)
+    assert st["converged"]
+    mp = Multipatch(dom)
+    jump, umax = _jump(mp, got)
+    assert jump <= 1e-9 * umax, (jump, umax)
+    rng = np.random.default_rng(0)
+    patches = rng.choice(dom.npatch, size=min(4, dom.npatch), replace=False)
+    for k in patches:
+        for i in _interior_rows(dom, int(k), rng, 6):
+            cols, vals, fi = assembly.row_stiffness_load(dom, int(k), i)
+            ku = float(vals @ got[k][cols])
+            scale = float(np.abs(vals) @ np.abs(got[k][cols])) + abs(fi)
+            assert abs(ku - fi) <= 1e-9 * scale, (k, i, ku, fi)

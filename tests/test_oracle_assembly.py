@@ -90,3 +90,21 @@ def test_load_integrates_f():
     g = 2 * np.pi ** 2 * np.outer(np.sin(np.pi * X), np.sin(np.pi * X))
     ref = 0.25 * w @ g @ w
     assert abs(f.sum() - ref) < 1e-5
+
+
+@pytest.mark.parametrize("dom", [W.annulus_6x6(4, 3, grid=(2, 2)),
+                                 W.random_quad_rhs(W.uneven_8x8(0, grid=(2, 2), nelems=(4, 8))),
+                                 W.cube_2x2x2(3, 2)])
+def test_single_row_equals_full_assembly(dom):
+    """The one-row oracle used for full-size checks equals the rows of the
+    full patch assembly (same Gauss rule, support-restricted)."""
+    for k in range(dom.npatch):
+        K, f, _ = assembly.assemble_patch(dom, k)
+        rng = np.random.default_rng(k)
+        for i in rng.integers(0, K.shape[0], 4):
+            cols, vals, fi = assembly.row_stiffness_load(dom, k, int(i))
+            ref = K[int(i)].toarray().ravel()
+            got = np.zeros_like(ref)
+            got[cols] = vals
+            assert np.abs(got - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max())
+            assert abs(fi - f[int(i)]) <= 1e-12 * max(1.0, abs(f[int(i)]))
