@@ -203,6 +203,39 @@ int ietidp_solve(ietidp_handle* h, const double* f, double* u_out, ietidp_stats*
 int ietidp_solve_host(ietidp_handle* h, const double* f_host, double* u_host,
                       ietidp_stats* stats);
 
+/* Batched solve: the dual PCG of ietidp_solve for n handles at once, in
+ * lockstep.  Each outer iteration runs the local Neumann solves of every
+ * patch of every handle in one kernel launch per degree specialisation, then
+ * one host synchronisation reads all dual residuals, then the
+ * preconditioners of the handles that continue run in one launch per
+ * specialisation.  Handles that converge leave the batch.  Patches are
+ * ordered longest first; block size and shared-memory budget of each merged
+ * launch are chosen by an autotuner that times its candidates once per launch
+ * shape (IETIDP_AUTOTUNE=0: 512 threads, full budget).  Every handle's result
+ * equals its own ietidp_solve up to rounding (the reduction order of dot
+ * products follows the block size).
+ * hs: n distinct handles on one device; f[i] device load of handle i (f or
+ * f[i] NULL: assembled load); u[i] device outputs (n_torn_i doubles);
+ * stats: n entries or NULL.  Runs on the stream of hs[0]; the other handles'
+ * streams are joined before and after.  Returns the first failing handle's
+ * code (all stats are filled). */
+int ietidp_solve_batch(ietidp_handle* const* hs, int n, const double* const* f, double* const* u,
+                       ietidp_stats* stats);
+/* Same with HOST buffers (copies in and out inside the call). */
+int ietidp_solve_batch_host(ietidp_handle* const* hs, int n, const double* const* f_host,
+                            double* const* u_host, ietidp_stats* stats);
+
+/* Autotuner decisions so far (process-wide): up to max_entries records of
+ * 10 ints {dim, p0, p1, p2, kind (0 specialised, 1 global-memory vectors,
+ * 2 run-time degree), mixed, waves, threads, smem bytes, CTAs per SM} into
+ * out (may be NULL); returns the number of decisions. */
+int ietidp_autotune_table(int* out, int max_entries);
+
+/* Kernels launched so far in this process by the solve entry points
+ * (ietidp_solve*, ietidp_vcycles*, the ietidp_apply_* probes); assembly and
+ * setup launches are not counted. */
+long long ietidp_kernel_launches(void);
+
 /* Apply `ncycles` V-cycles (Sec. 4 multigrid) to every patch's Neumann
  * hierarchy in one batched launch each: x <- x + V(b - A x), with b and x
  * device vectors in patch layout.  Used to measure V-cycle throughput. */

@@ -14,7 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libietidp.so")
-SOURCES = ["setup_kernels.cu", "solver_kernels.cu", "dual_kernels.cu", "ietidp_host.cu", "ietidp_server.cu",
+SOURCES = ["setup_kernels.cu", "solver_kernels.cu", "dual_kernels.cu", "ietidp_host.cu", "ietidp_engine.cu",
+           "ietidp_server.cu",
            "solver_dispatch.cu"] + sorted(f for f in os.listdir(SRC) if f.startswith("solver_t_"))
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]

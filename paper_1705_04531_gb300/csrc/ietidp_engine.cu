@@ -1,0 +1,840 @@
+// Batched solve engine: the dual PCG of Sec. 2 (F lambda = d with the scaled
+// Dirichlet preconditioner, Eq. 4) for several jobs -- a job is one handle and
+// one right-hand side -- advanced in lockstep.  One tick is one outer
+// iteration of every job:
+//
+//   stage A  local Neumann solves  (u0 = K~^{-1} f, F p, or the recovery
+//            u = K~^{-1}(f - B^T lambda), whichever each job needs next);
+//            all patches of all jobs run in ONE launch per kernel
+//            specialisation
+//   sync     one stream synchronisation reads every job's dual residual
+//   stage B  scaled Dirichlet preconditioner of the jobs that continue,
+//            again one launch per specialisation over all their patches
+//
+// Jobs join and leave the set between ticks (ietidp_solve is a batch of one;
+// the server feeds the engine as requests are admitted).  The patch-to-CTA
+// order of a merged launch is longest-first, and the block size and
+// shared-memory budget of each merged launch are picked by an autotuner that
+// times the candidate configurations once per launch shape.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <numeric>
+#include <tuple>
+#include <vector>
+
+#include "host_internal.h"
+#include "engine.h"
+
+using namespace ieti_host;
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// autotuner
+// ---------------------------------------------------------------------------
+struct TuneKey {
+    int dim, p0, p1, p2, kind, mixed;   // kind: 0 specialised, 1 global-memory vectors, 2 run-time degree
+    int waves;                          // ceil(slots / SMs)
+    long long max_cost;                 // largest patch (rows x stencil)
+    bool operator<(const TuneKey& o) const {
+        return std::tie(dim, p0, p1, p2, kind, mixed, waves, max_cost) <
+               std::tie(o.dim, o.p0, o.p1, o.p2, o.kind, o.mixed, o.waves, o.max_cost);
+    }
+};
+
+struct TuneCfg {
+    int threads;
+    size_t smem;
+    int ctas_per_sm;
+    float ms;
+};
+
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneCfg> g_tune;
+
+bool autotune_enabled() {
+    const char* e = std::getenv("IETIDP_AUTOTUNE");
+    return !(e && e[0] == '0');
+}
+
+int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+// one merged launch: the slots of every job that share a kernel specialisation
+struct MGroup {
+    int dim = 0, p0 = 0, p1 = 0, p2 = 0, kind = 0, mixed = 0;
+    std::vector<SlotDesc> s;
+    std::vector<long long> cost;
+    size_t smem = 0;       // shared memory of the handles' own plan (max)
+    size_t smem_min = 0;   // shared memory the kernel cannot do without (max)
+    TuneCfg cfg{512, 0, 1, 0.f};
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// engine state
+// ---------------------------------------------------------------------------
+struct Staging {   // pinned and device copies of one launch stage's arguments and slots
+    SolveArgs* h_args = nullptr;
+    SolveArgs* d_args = nullptr;
+    size_t cap_args = 0;
+    SlotDesc* h_slots = nullptr;
+    SlotDesc* d_slots = nullptr;
+    size_t cap_slots = 0;
+};
+
+struct ieti_engine {
+    cudaStream_t st = nullptr;
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> join;
+    cudaEvent_t fork = nullptr, e0 = nullptr, e1 = nullptr;   // e0/e1: bracket of stage A
+    cudaEvent_t t0 = nullptr, t1 = nullptr;                   // autotuner timing
+    Staging stA, stB, stT;
+    double* h_rb = nullptr;   // pinned read-back, one block per job
+    size_t cap_rb = 0;
+};
+
+namespace {
+
+int reserve(ieti_engine* E, Staging& S, size_t nargs, size_t nslots) {
+    if (nargs <= S.cap_args && nslots <= S.cap_slots) return IETIDP_OK;
+    // earlier copies from the pinned buffers must have completed
+    CU(cudaStreamSynchronize(E->st));
+    size_t na = std::max(nargs, 2 * S.cap_args), ns = std::max(nslots, 2 * S.cap_slots);
+    if (S.h_args) cudaFreeHost(S.h_args);
+    if (S.h_slots) cudaFreeHost(S.h_slots);
+    if (S.d_args) cudaFreeAsync(S.d_args, E->st);
+    if (S.d_slots) cudaFreeAsync(S.d_slots, E->st);
+    S = Staging{};
+    CU(cudaMallocHost((void**)&S.h_args, sizeof(SolveArgs) * na));
+    CU(cudaMallocHost((void**)&S.h_slots, sizeof(SlotDesc) * ns));
+    CU(cudaMallocAsync((void**)&S.d_args, sizeof(SolveArgs) * na, E->st));
+    CU(cudaMallocAsync((void**)&S.d_slots, sizeof(SlotDesc) * ns, E->st));
+    S.cap_args = na;
+    S.cap_slots = ns;
+    return IETIDP_OK;
+}
+
+void free_staging(ieti_engine* E, Staging& S) {
+    if (S.h_args) cudaFreeHost(S.h_args);
+    if (S.h_slots) cudaFreeHost(S.h_slots);
+    if (S.d_args) cudaFreeAsync(S.d_args, E->st);
+    if (S.d_slots) cudaFreeAsync(S.d_slots, E->st);
+    S = Staging{};
+}
+
+int ensure_side(ieti_engine* E, size_t n) {
+    while (E->side.size() < std::min<size_t>(n, 8)) {
+        cudaStream_t s;
+        cudaEvent_t ev;
+        CU(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        CU(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        E->side.push_back(s);
+        E->join.push_back(ev);
+    }
+    return IETIDP_OK;
+}
+
+cudaError_t launch_cfg(const SolveArgs& a, const MGroup& g, const TuneCfg& c, cudaStream_t st) {
+    SolveArgs b = a;
+    b.smem_bytes = c.smem;
+    if (g.kind == 2) return launch_solve(b, c.threads, st);
+    return launch_solve_variant(b, g.dim, g.p0, g.p1, g.p2, c.threads, st, g.kind == 1);
+}
+
+// candidate configurations of a merged launch: 512 threads with the full
+// budget, or fewer threads with a budget that lets 2 or 3 CTAs share an SM
+std::vector<TuneCfg> candidates(const MGroup& g) {
+    std::vector<TuneCfg> c;
+    c.push_back(TuneCfg{512, g.smem, 1, 0.f});
+    if (g.kind == 2) return c;
+    const int want[2] = {2, 3};
+    const int thr[2] = {256, 128};
+    for (int k = 0; k < 2; ++k) {
+        // largest budget (in 4 KB steps) at which `want` CTAs fit on an SM
+        for (size_t b = std::min(g.smem, (size_t)kSmemCap / want[k]); b >= 16 * 1024; b -= 4 * 1024) {
+            if (b < g.smem_min) break;
+            int occ = solve_variant_ctas_per_sm(g.dim, g.p0, g.p1, g.p2, g.mixed, g.kind == 1, thr[k], b);
+            if (occ >= want[k]) {
+                c.push_back(TuneCfg{thr[k], b, occ, 0.f});
+                break;
+            }
+        }
+    }
+    return c;
+}
+
+// time each candidate on one V-cycle per slot (zero data, same work as a
+// real launch) and keep the fastest; cached per launch shape
+int tune(ieti_engine* E, MGroup& g, const std::vector<ietidp_handle*>& hs, long long* nlaunch) {
+    g.cfg = TuneCfg{512, g.smem, 1, 0.f};
+    if (g.kind == 2 || !autotune_enabled()) return IETIDP_OK;
+    TuneKey key{g.dim, g.p0, g.p1, g.p2, g.kind, g.mixed,
+                (int)((g.s.size() + sm_count() - 1) / sm_count()),
+                *std::max_element(g.cost.begin(), g.cost.end())};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            if (it->second.smem >= g.smem_min) {
+                g.cfg = it->second;
+                g.cfg.smem = std::min(g.cfg.smem, g.smem);
+            }
+            return IETIDP_OK;
+        }
+    }
+    std::vector<TuneCfg> cand = candidates(g);
+    if (cand.size() > 1) {
+        // scratch input/output vectors of every handle (zero)
+        long long tot = 0;
+        std::vector<long long> off(hs.size());
+        for (size_t i = 0; i < hs.size(); ++i) {
+            off[i] = tot;
+            tot += hs[i]->prob->ntorn;
+        }
+        double* buf = nullptr;
+        CU(cudaMallocAsync((void**)&buf, sizeof(double) * 2 * tot, E->st));
+        CU(cudaMemsetAsync(buf, 0, sizeof(double) * 2 * tot, E->st));
+        CHK(reserve(E, E->stT, hs.size(), g.s.size()));
+        for (size_t i = 0; i < hs.size(); ++i) {
+            SolveArgs a = ieti_solve_args(hs[i], MODE_VCYCLE, buf + off[i], buf + tot + off[i], 0.0, 0, nullptr);
+            a.ncycles = 1;
+            E->stT.h_args[i] = a;
+        }
+        std::copy(g.s.begin(), g.s.end(), E->stT.h_slots);
+        CU(cudaMemcpyAsync(E->stT.d_args, E->stT.h_args, sizeof(SolveArgs) * hs.size(), cudaMemcpyHostToDevice,
+                           E->st));
+        CU(cudaMemcpyAsync(E->stT.d_slots, E->stT.h_slots, sizeof(SlotDesc) * g.s.size(), cudaMemcpyHostToDevice,
+                           E->st));
+        SolveArgs a0 = E->stT.h_args[0];
+        a0.batch = E->stT.d_args;
+        a0.slots = E->stT.d_slots;
+        a0.nslots = (int)g.s.size();
+        a0.mixed = g.mixed;
+        float best = 1e30f;
+        size_t bi = 0;
+        for (size_t c = 0; c < cand.size(); ++c) {
+            cudaError_t e = launch_cfg(a0, g, cand[c], E->st);   // warm-up
+            if (e == cudaSuccess) {
+                cudaEventRecord(E->t0, E->st);
+                e = launch_cfg(a0, g, cand[c], E->st);
+                cudaEventRecord(E->t1, E->st);
+            }
+            *nlaunch += 2;
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                continue;
+            }
+            CU(cudaEventSynchronize(E->t1));
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, E->t0, E->t1);
+            cand[c].ms = ms;
+            if (ms < best) {
+                best = ms;
+                bi = c;
+            }
+        }
+        CU(cudaFreeAsync(buf, E->st));
+        g.cfg = cand[bi];
+    }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = g.cfg;
+    return IETIDP_OK;
+}
+
+// one local-solve stage: every item's slots, merged per specialisation
+int merged_launch(ieti_engine* E, Staging& S, std::vector<std::pair<ietidp_handle*, SolveArgs>>& items,
+                  long long* nlaunch) {
+    if (items.empty()) return IETIDP_OK;
+    std::map<std::tuple<int, int, int, int, int, int>, MGroup> by;
+    for (size_t i = 0; i < items.size(); ++i) {
+        ietidp_handle* h = items[i].first;
+        const int mixed = h->opt.precision == IETIDP_PREC_MIXED;
+        for (const SlotGroup& sg : h->gpatch) {
+            const int kind = sg.generic ? 2 : (sg.xg ? 1 : 0);
+            MGroup& m = by[std::make_tuple(sg.dim, sg.p0, sg.p1, sg.p2, kind, mixed)];
+            m.dim = sg.dim;
+            m.p0 = sg.p0;
+            m.p1 = sg.p1;
+            m.p2 = sg.p2;
+            m.kind = kind;
+            m.mixed = mixed;
+            m.smem = std::max(m.smem, sg.smem);
+            for (SlotDesc sd : sg.hs) {
+                sd.handle = (int)i;
+                const PatchDesc& P = h->pd[sd.patch];
+                m.s.push_back(sd);
+                m.cost.push_back((long long)P.n * P.lev[P.L - 1].S);
+                m.smem_min = std::max(m.smem_min, kind == 1 ? solve_smem_tables(P) : solve_smem_min(P, mixed));
+            }
+        }
+    }
+    std::vector<ietidp_handle*> hs(items.size());
+    for (size_t i = 0; i < items.size(); ++i) hs[i] = items[i].first;
+    size_t total = 0;
+    for (auto& kv : by) {
+        MGroup& m = kv.second;
+        // longest patches first, so that uneven batches finish together
+        std::vector<size_t> ord(m.s.size());
+        std::iota(ord.begin(), ord.end(), 0);
+        std::stable_sort(ord.begin(), ord.end(), [&](size_t x, size_t y) { return m.cost[x] > m.cost[y]; });
+        std::vector<SlotDesc> s2(m.s.size());
+        std::vector<long long> c2(m.s.size());
+        for (size_t k = 0; k < ord.size(); ++k) {
+            s2[k] = m.s[ord[k]];
+            c2[k] = m.cost[ord[k]];
+        }
+        m.s.swap(s2);
+        m.cost.swap(c2);
+        CHK(tune(E, m, hs, nlaunch));
+        total += m.s.size();
+    }
+    CHK(reserve(E, S, items.size(), total));
+    for (size_t i = 0; i < items.size(); ++i) S.h_args[i] = items[i].second;
+    size_t off = 0;
+    for (auto& kv : by) {
+        std::copy(kv.second.s.begin(), kv.second.s.end(), S.h_slots + off);
+        off += kv.second.s.size();
+    }
+    CU(cudaMemcpyAsync(S.d_args, S.h_args, sizeof(SolveArgs) * items.size(), cudaMemcpyHostToDevice, E->st));
+    CU(cudaMemcpyAsync(S.d_slots, S.h_slots, sizeof(SlotDesc) * total, cudaMemcpyHostToDevice, E->st));
+    SolveArgs a0 = items[0].second;
+    a0.batch = S.d_args;
+    const bool multi = by.size() > 1;
+    if (multi) {
+        CHK(ensure_side(E, by.size()));
+        CU(cudaEventRecord(E->fork, E->st));
+    }
+    off = 0;
+    size_t gi = 0;
+    for (auto& kv : by) {
+        MGroup& m = kv.second;
+        a0.slots = S.d_slots + off;
+        a0.nslots = (int)m.s.size();
+        a0.mixed = m.mixed;
+        off += m.s.size();
+        cudaStream_t s = E->st;
+        if (multi) {
+            s = E->side[gi % E->side.size()];
+            CU(cudaStreamWaitEvent(s, E->fork, 0));
+        }
+        cudaError_t e = launch_cfg(a0, m, m.cfg, s);
+        *nlaunch += 1;
+        if (e != cudaSuccess) return fail(IETIDP_E_CUDA, std::string("local solve kernel: ") + cudaGetErrorString(e));
+        ++gi;
+    }
+    if (multi) {
+        for (size_t i = 0; i < std::min(by.size(), E->side.size()); ++i) {
+            CU(cudaEventRecord(E->join[i], E->side[i]));
+            CU(cudaStreamWaitEvent(E->st, E->join[i], 0));
+        }
+    }
+    return IETIDP_OK;
+}
+
+double lanczos_kappa(const std::vector<double>& al, const std::vector<double>& be) {
+    int n = (int)al.size();
+    if (n == 0) return 1.0;
+    // eigenvalues of the Lanczos tridiagonal matrix of the CG coefficients by
+    // bisection on Sturm sequence counts
+    std::vector<double> dd(n), ee(n, 0.0);
+    for (int k = 0; k < n; ++k) {
+        dd[k] = 1.0 / al[k] + (k > 0 ? be[k - 1] / al[k - 1] : 0.0);
+        if (k < n - 1 && k < (int)be.size()) ee[k] = std::sqrt(std::max(0.0, be[k])) / al[k];
+    }
+    double lo = 1e300, hi = -1e300;
+    for (int k = 0; k < n; ++k) {
+        double rad = std::fabs(k > 0 ? ee[k - 1] : 0.0) + std::fabs(ee[k]);
+        lo = std::min(lo, dd[k] - rad);
+        hi = std::max(hi, dd[k] + rad);
+    }
+    auto count_below = [&](double x) {
+        int c = 0;
+        double q = 1.0;
+        for (int k = 0; k < n; ++k) {
+            double e2 = k > 0 ? ee[k - 1] * ee[k - 1] : 0.0;
+            q = dd[k] - x - (k > 0 ? e2 / q : 0.0);
+            if (q == 0.0) q = -1e-300;
+            if (q < 0) ++c;
+        }
+        return c;
+    };
+    auto eig = [&](int idx) {
+        double a = lo, b = hi;
+        for (int it = 0; it < 200; ++it) {
+            double mid = 0.5 * (a + b);
+            if (count_below(mid) > idx) b = mid;
+            else a = mid;
+        }
+        return 0.5 * (a + b);
+    };
+    return eig(n - 1) / eig(0);
+}
+
+constexpr int kRb = 16;   // read-back doubles per job before its CG history
+
+// small per-job launches count for the job and for the process-wide counter
+void count(EngineJob& j, long long k) {
+    j.S.launches += k;
+    ieti_host::g_kernel_launches += k;
+}
+
+size_t rb_stride(const ietidp_handle* h) { return kRb + 2 * (size_t)(h->opt.maxit_outer + 1); }
+
+// small per-job launches (one job, engine stream)
+#define LCHK(x)                                                                 \
+    do {                                                                        \
+        cudaError_t e_ = (x);                                                   \
+        if (e_ != cudaSuccess) return fail(IETIDP_E_CUDA, cudaGetErrorString(e_)); \
+    } while (0)
+
+int primal(ietidp_handle* h, const double* g, cudaStream_t st, EngineJob& j) {
+    LCHK(launch_primal_restrict(h->d_pd, h->nrows, h->crow_patch, h->crow_local, h->phi, g, h->rloc, st));
+    LCHK(launch_coarse_solve(h->npi, h->nrows, h->crow_glob, h->gptr, h->glist, h->Linv, h->rloc, h->upi, h->uloc,
+                             st));
+    count(j, (h->nrows > 0) + (h->npi > 0));
+    return IETIDP_OK;
+}
+
+void finish(EngineJob& j) {
+    const ietidp_handle* h = j.h;
+    auto t1 = std::chrono::steady_clock::now();
+    ietidp_stats& S = j.S;
+    S.outer_it = j.it;
+    S.converged = j.conv && !(j.flags & IETI_FLAG_NOT_CONVERGED);
+    S.kappa = lanczos_kappa(j.al, j.be);
+    S.vcycles = j.vs[0];
+    S.vcycle_dofs = j.vs[1];
+    S.inner_its = j.vs[2];
+    if (j.vs[4] > 0) {
+        S.inner_it_avg = (double)j.vs[2] / (double)j.vs[4];
+        S.inner_it_max = (int)j.vs[3];
+    }
+    S.basis_it_avg = h->basis_it_avg;
+    S.basis_it_max = h->basis_it_max;
+    S.t_setup_ms = h->t_setup_ms;
+    S.t_solve_ms = std::chrono::duration<double, std::milli>(t1 - j.t0).count();
+    if (j.rc == IETIDP_OK) {
+        if (j.flags & IETI_FLAG_BREAKDOWN) {
+            j.rc = IETIDP_E_BREAKDOWN;
+            j.err = "CG breakdown in a local solve";
+        } else if (!S.converged) {
+            j.rc = IETIDP_E_NOT_CONVERGED;
+            j.err = "solver did not converge";
+        }
+    }
+    j.phase = EngineJob::DONE;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// engine API (engine.h)
+// ---------------------------------------------------------------------------
+int ieti_engine_create(cudaStream_t st, ieti_engine** out) {
+    auto* E = new ieti_engine();
+    E->st = st;
+    cudaError_t e = cudaEventCreateWithFlags(&E->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreate(&E->e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&E->e1);
+    if (e == cudaSuccess) e = cudaEventCreate(&E->t0);
+    if (e == cudaSuccess) e = cudaEventCreate(&E->t1);
+    if (e != cudaSuccess) {
+        delete E;
+        return fail(IETIDP_E_CUDA, std::string("engine events: ") + cudaGetErrorString(e));
+    }
+    *out = E;
+    return IETIDP_OK;
+}
+
+void ieti_engine_destroy(ieti_engine* E) {
+    if (!E) return;
+    cudaStreamSynchronize(E->st);
+    free_staging(E, E->stA);
+    free_staging(E, E->stB);
+    free_staging(E, E->stT);
+    cudaStreamSynchronize(E->st);
+    if (E->h_rb) cudaFreeHost(E->h_rb);
+    for (auto s : E->side) cudaStreamDestroy(s);
+    for (auto ev : E->join) cudaEventDestroy(ev);
+    if (E->fork) cudaEventDestroy(E->fork);
+    if (E->e0) cudaEventDestroy(E->e0);
+    if (E->e1) cudaEventDestroy(E->e1);
+    if (E->t0) cudaEventDestroy(E->t0);
+    if (E->t1) cudaEventDestroy(E->t1);
+    delete E;
+}
+
+cudaStream_t ieti_engine_stream(const ieti_engine* E) { return E->st; }
+
+void ieti_engine_job_init(EngineJob& j, ietidp_handle* h, const double* f, double* u) {
+    j = EngineJob{};
+    j.h = h;
+    j.f = f ? f : h->prob->f;
+    j.u = u;
+    j.t0 = std::chrono::steady_clock::now();
+}
+
+int ieti_engine_tick(ieti_engine* E, std::vector<EngineJob*>& jobs) {
+    cudaStream_t st = E->st;
+    // read-back area
+    size_t need = 0;
+    std::vector<size_t> rbo(jobs.size());
+    for (size_t i = 0; i < jobs.size(); ++i) {
+        rbo[i] = need;
+        need += rb_stride(jobs[i]->h);
+    }
+    if (need > E->cap_rb) {
+        CU(cudaStreamSynchronize(st));
+        if (E->h_rb) cudaFreeHost(E->h_rb);
+        E->h_rb = nullptr;
+        E->cap_rb = 0;
+        CU(cudaMallocHost((void**)&E->h_rb, sizeof(double) * std::max(need, (size_t)256)));
+        E->cap_rb = std::max(need, (size_t)256);
+    }
+    long long nl = 0;
+    // ---- stage A: local Neumann solves --------------------------------------
+    std::vector<std::pair<ietidp_handle*, SolveArgs>> A;
+    std::vector<EngineJob*> inA;
+    for (EngineJob* j : jobs) {
+        ietidp_handle* h = j->h;
+        if (j->phase == EngineJob::INIT) {
+            CU(cudaMemsetAsync(h->flags, 0, sizeof(int), st));
+            CU(cudaMemsetAsync(h->vst, 0, sizeof(long long) * 8, st));
+            CHK(primal(h, j->f, st, *j));
+            A.emplace_back(h, ieti_solve_args(h, MODE_NEUMANN, j->f, j->u, h->opt.tol_inner, h->opt.maxit_inner,
+                                              h->vst));
+        } else if (j->phase == EngineJob::ITER) {
+            LCHK(launch_bt(h->dual, h->p, h->gF, 0, st));
+            count(*j, 1);
+            CHK(primal(h, h->gF, st, *j));
+            A.emplace_back(h, ieti_solve_args(h, MODE_NEUMANN, h->gF, h->uF, h->opt.tol_inner, h->opt.maxit_inner,
+                                              h->vst));
+        } else if (j->phase == EngineJob::RECOVER) {
+            LCHK(launch_bt(h->dual, h->lam, h->tmp, 0, st));
+            LCHK(launch_axpy_torn(h->prob->ntorn, j->f, -1.0, h->tmp, h->gR, st));
+            count(*j, 2);
+            CHK(primal(h, h->gR, st, *j));
+            A.emplace_back(h, ieti_solve_args(h, MODE_NEUMANN, h->gR, j->u, h->opt.tol_inner, h->opt.maxit_inner,
+                                              h->vst));
+        } else {
+            continue;
+        }
+        inA.push_back(j);
+    }
+    if (!A.empty()) {
+        long long n0 = nl;
+        CU(cudaEventRecord(E->e0, st));
+        CHK(merged_launch(E, E->stA, A, &nl));
+        CU(cudaEventRecord(E->e1, st));
+        ieti_host::g_kernel_launches += nl - n0;
+        for (EngineJob* j : inA) {
+            j->S.launches += nl - n0;
+            j->S.neumann_launches += 1;
+        }
+    }
+    for (size_t i = 0; i < jobs.size(); ++i) {
+        EngineJob* j = jobs[i];
+        ietidp_handle* h = j->h;
+        double* rb = E->h_rb + rbo[i];
+        if (j->phase == EngineJob::INIT) {
+            if (h->nlam > 0) {
+                LCHK(launch_b(h->dual, j->u, h->d, 0, st));
+                LCHK(launch_jump_scale(h->dual, j->u, h->scal, st));
+                LCHK(launch_outer_init(h->nlam, h->d, h->lam, h->r, h->state, st));
+                count(*j, 3);
+                CU(cudaMemcpyAsync(rb, h->state + 5, sizeof(double), cudaMemcpyDeviceToHost, st));
+                CU(cudaMemcpyAsync(rb + 1, h->scal, sizeof(double), cudaMemcpyDeviceToHost, st));
+            }
+            CU(cudaMemcpyAsync(rb + 2, h->flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+            CU(cudaMemcpyAsync(rb + 8, h->vst, sizeof(long long) * 8, cudaMemcpyDeviceToHost, st));
+        } else if (j->phase == EngineJob::ITER) {
+            LCHK(launch_b(h->dual, h->uF, h->q, 0, st));
+            LCHK(launch_outer_step1(h->nlam, h->p, h->q, h->lam, h->r, h->state, h->hist, j->it - 1, st));
+            count(*j, 2);
+            CU(cudaMemcpyAsync(rb, h->state + 4, sizeof(double), cudaMemcpyDeviceToHost, st));
+        } else if (j->phase == EngineJob::RECOVER) {
+            CU(cudaMemcpyAsync(rb + 2, h->flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+            CU(cudaMemcpyAsync(rb + 8, h->vst, sizeof(long long) * 8, cudaMemcpyDeviceToHost, st));
+            if (j->it > 0)
+                CU(cudaMemcpyAsync(rb + kRb, h->hist, sizeof(double) * 2 * j->it, cudaMemcpyDeviceToHost, st));
+        }
+    }
+    CU(cudaStreamSynchronize(st));
+    float msA = 0.f;
+    if (!A.empty()) cudaEventElapsedTime(&msA, E->e0, E->e1);
+    for (EngineJob* j : inA) j->S.neumann_ms += msA;
+    // ---- host decisions --------------------------------------------------------
+    for (size_t i = 0; i < jobs.size(); ++i) {
+        EngineJob* j = jobs[i];
+        ietidp_handle* h = j->h;
+        const double* rb = E->h_rb + rbo[i];
+        if (j->phase == EngineJob::INIT || j->phase == EngineJob::RECOVER) {
+            std::memcpy(&j->flags, rb + 2, sizeof(int));
+            std::memcpy(j->vs, rb + 8, sizeof(long long) * 8);
+        }
+        if (j->phase == EngineJob::INIT) {
+            if (h->nlam == 0) {
+                finish(*j);
+                continue;
+            }
+            j->dd = rb[0];
+            const double sc2 = rb[1];
+            if (!std::isfinite(j->dd)) {
+                j->rc = IETIDP_E_NONFINITE;
+                j->err = "non-finite dual right-hand side";
+                finish(*j);
+                continue;
+            }
+            j->S.d_norm = std::sqrt(j->dd);
+            j->S.d_scale = std::sqrt(sc2);
+            const double tol = h->opt.tol_outer;
+            if (j->S.d_norm <= tol * j->S.d_scale) {
+                // the jump of u0 vanishes to rounding: lambda = 0
+                j->conv = true;
+                finish(*j);
+                continue;
+            }
+            j->conv = false;
+            j->thr2 = tol * tol * j->dd;
+            j->phase = EngineJob::PRECF;
+        } else if (j->phase == EngineJob::ITER) {
+            const double rr = rb[0];
+            if (!std::isfinite(rr)) {
+                j->rc = IETIDP_E_NONFINITE;
+                j->err = "non-finite dual residual";
+                finish(*j);
+                continue;
+            }
+            j->S.rel_res = std::sqrt(rr / j->dd);
+            if (rr <= j->thr2) {
+                j->conv = true;
+                j->phase = EngineJob::RECOVER;
+            } else if (j->it >= h->opt.maxit_outer) {
+                j->phase = EngineJob::RECOVER;
+            } else {
+                j->phase = EngineJob::PREC;
+            }
+        } else if (j->phase == EngineJob::RECOVER) {
+            for (int k = 0; k < j->it; ++k) {
+                j->al.push_back(rb[kRb + 2 * k]);
+                if (k < j->it - 1) j->be.push_back(rb[kRb + 2 * k + 1]);
+            }
+            finish(*j);
+        }
+    }
+    // ---- stage B: scaled Dirichlet preconditioner ---------------------------------
+    std::vector<std::pair<ietidp_handle*, SolveArgs>> B;
+    std::vector<EngineJob*> inB;
+    for (EngineJob* j : jobs) {
+        if (j->phase != EngineJob::PRECF && j->phase != EngineJob::PREC) continue;
+        ietidp_handle* h = j->h;
+        LCHK(launch_bt(h->dual, h->r, h->vS, 1, st));
+        count(*j, 1);
+        B.emplace_back(h, ieti_solve_args(h, MODE_SCHUR, h->vS, h->wS, 0.0, 0, h->vst));
+        inB.push_back(j);
+    }
+    if (!B.empty()) {
+        long long n0 = nl;
+        CHK(merged_launch(E, E->stB, B, &nl));
+        ieti_host::g_kernel_launches += nl - n0;
+        for (EngineJob* j : inB) j->S.launches += nl - n0;
+    }
+    for (EngineJob* j : inB) {
+        ietidp_handle* h = j->h;
+        LCHK(launch_b(h->dual, h->wS, h->z, 1, st));
+        if (j->phase == EngineJob::PRECF) {
+            LCHK(launch_outer_first(h->nlam, h->r, h->z, h->p, h->state, st));
+            j->it = 1;
+        } else {
+            LCHK(launch_outer_step2(h->nlam, h->r, h->z, h->p, h->state, h->hist, j->it - 1, st));
+            j->it += 1;
+        }
+        count(*j, 2);
+        j->phase = EngineJob::ITER;
+    }
+    return IETIDP_OK;
+}
+
+int ieti_engine_run(ieti_engine* E, std::vector<EngineJob*>& jobs) {
+    for (;;) {
+        bool any = false;
+        for (EngineJob* j : jobs) any = any || j->phase != EngineJob::DONE;
+        if (!any) return IETIDP_OK;
+        std::vector<EngineJob*> live;
+        for (EngineJob* j : jobs)
+            if (j->phase != EngineJob::DONE) live.push_back(j);
+        CHK(ieti_engine_tick(E, live));
+    }
+}
+
+extern "C" int ietidp_autotune_table(int* out, int max_entries) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    int n = 0;
+    for (const auto& kv : g_tune) {
+        if (out && n < max_entries) {
+            int* o = out + 10 * n;
+            o[0] = kv.first.dim;
+            o[1] = kv.first.p0;
+            o[2] = kv.first.p1;
+            o[3] = kv.first.p2;
+            o[4] = kv.first.kind;
+            o[5] = kv.first.mixed;
+            o[6] = kv.first.waves;
+            o[7] = kv.second.threads;
+            o[8] = (int)kv.second.smem;
+            o[9] = kv.second.ctas_per_sm;
+        }
+        ++n;
+    }
+    return n;
+}
+
+// ---------------------------------------------------------------------------
+// public solve entry points
+// ---------------------------------------------------------------------------
+namespace {
+
+int engine_of(ietidp_handle* h, ieti_engine** E) {
+    if (!h->engine) CHK(ieti_engine_create(h->st, &h->engine));
+    *E = h->engine;
+    return IETIDP_OK;
+}
+
+// run jobs on the engine of hs[0]; the other handles' streams are joined
+// before and after, so work the caller queued on them stays ordered
+int run_jobs(ietidp_handle* const* hs, int n, std::vector<EngineJob>& jobs, bool host,
+             const double* const* f_host, double* const* u_host) {
+    ieti_engine* E = nullptr;
+    CHK(engine_of(hs[0], &E));
+    cudaStream_t st = E->st;
+    std::vector<cudaEvent_t> evs;
+    auto cleanup = [&]() {
+        for (auto ev : evs) cudaEventDestroy(ev);
+    };
+    for (int i = 1; i < n; ++i) {
+        if (hs[i]->st == st) continue;
+        cudaEvent_t ev;
+        CU(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        evs.push_back(ev);
+        CU(cudaEventRecord(ev, hs[i]->st));
+        CU(cudaStreamWaitEvent(st, ev, 0));
+    }
+    if (host)
+        for (int i = 0; i < n; ++i)
+            if (f_host && f_host[i]) {
+                int rc = IETIDP_OK;
+                cudaError_t e = cudaMemcpyAsync(hs[i]->fH, f_host[i], sizeof(double) * hs[i]->prob->ntorn,
+                                                cudaMemcpyHostToDevice, st);
+                if (e != cudaSuccess) rc = fail(IETIDP_E_CUDA, std::string("H2D: ") + cudaGetErrorString(e));
+                if (rc != IETIDP_OK) {
+                    cleanup();
+                    return rc;
+                }
+            }
+    std::vector<EngineJob*> ptr;
+    for (auto& j : jobs) ptr.push_back(&j);
+    int rc = ieti_engine_run(E, ptr);
+    if (rc == IETIDP_OK && host) {
+        for (int i = 0; i < n; ++i) {
+            if (jobs[i].rc != IETIDP_OK && jobs[i].rc != IETIDP_E_NOT_CONVERGED) continue;
+            cudaError_t e = cudaMemcpyAsync(u_host[i], hs[i]->uH, sizeof(double) * hs[i]->prob->ntorn,
+                                            cudaMemcpyDeviceToHost, st);
+            if (e != cudaSuccess) {
+                rc = fail(IETIDP_E_CUDA, std::string("D2H: ") + cudaGetErrorString(e));
+                break;
+            }
+        }
+        if (rc == IETIDP_OK) {
+            cudaError_t e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) rc = fail(IETIDP_E_CUDA, cudaGetErrorString(e));
+        }
+    }
+    // later work on the other handles' streams waits for the batch
+    if (!evs.empty()) {
+        cudaEvent_t done = evs[0];
+        cudaEventRecord(done, st);
+        for (int i = 1; i < n; ++i)
+            if (hs[i]->st != st) cudaStreamWaitEvent(hs[i]->st, done, 0);
+    }
+    cleanup();
+    return rc;
+}
+
+int check_batch(ietidp_handle* const* hs, int n, double* const* u) {
+    if (!hs || n < 1 || !u) return fail(IETIDP_E_INVALID_ARG, "null argument");
+    for (int i = 0; i < n; ++i) {
+        if (!hs[i] || !u[i]) return fail(IETIDP_E_INVALID_ARG, "null handle or output in batch");
+        for (int k = 0; k < i; ++k)
+            if (hs[k] == hs[i]) return fail(IETIDP_E_INVALID_ARG, "a handle appears twice in one batch");
+        if (hs[i]->device != hs[0]->device) return fail(IETIDP_E_INVALID_ARG, "batch spans several devices");
+    }
+    return IETIDP_OK;
+}
+
+int report(std::vector<EngineJob>& jobs, ietidp_stats* stats) {
+    int first = IETIDP_OK;
+    std::string err;
+    for (size_t i = 0; i < jobs.size(); ++i) {
+        if (stats) stats[i] = jobs[i].S;
+        if (first == IETIDP_OK && jobs[i].rc != IETIDP_OK) {
+            first = jobs[i].rc;
+            err = jobs.size() > 1 ? "job " + std::to_string(i) + ": " + jobs[i].err : jobs[i].err;
+        }
+    }
+    if (first != IETIDP_OK) return fail(first, err);
+    return IETIDP_OK;
+}
+
+}  // namespace
+
+extern "C" int ietidp_solve(ietidp_handle* h, const double* f, double* u_out, ietidp_stats* stats) {
+    if (!h || !u_out) return fail(IETIDP_E_INVALID_ARG, "null argument");
+    std::vector<EngineJob> jobs(1);
+    ieti_engine_job_init(jobs[0], h, f, u_out);
+    CHK(run_jobs(&h, 1, jobs, false, nullptr, nullptr));
+    return report(jobs, stats);
+}
+
+extern "C" int ietidp_solve_host(ietidp_handle* h, const double* f_host, double* u_host, ietidp_stats* stats) {
+    if (!h || !u_host) return fail(IETIDP_E_INVALID_ARG, "null argument");
+    std::vector<EngineJob> jobs(1);
+    ieti_engine_job_init(jobs[0], h, f_host ? h->fH : nullptr, h->uH);
+    CHK(run_jobs(&h, 1, jobs, true, &f_host, &u_host));
+    return report(jobs, stats);
+}
+
+extern "C" int ietidp_solve_batch(ietidp_handle* const* hs, int n, const double* const* f, double* const* u,
+                                  ietidp_stats* stats) {
+    CHK(check_batch(hs, n, u));
+    std::vector<EngineJob> jobs(n);
+    for (int i = 0; i < n; ++i) ieti_engine_job_init(jobs[i], hs[i], f ? f[i] : nullptr, u[i]);
+    CHK(run_jobs(hs, n, jobs, false, nullptr, nullptr));
+    return report(jobs, stats);
+}
+
+extern "C" int ietidp_solve_batch_host(ietidp_handle* const* hs, int n, const double* const* f_host,
+                                       double* const* u_host, ietidp_stats* stats) {
+    CHK(check_batch(hs, n, u_host));
+    std::vector<EngineJob> jobs(n);
+    for (int i = 0; i < n; ++i)
+        ieti_engine_job_init(jobs[i], hs[i], (f_host && f_host[i]) ? hs[i]->fH : nullptr, hs[i]->uH);
+    CHK(run_jobs(hs, n, jobs, true, f_host, u_host));
+    return report(jobs, stats);
+}

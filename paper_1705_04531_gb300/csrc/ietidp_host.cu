@@ -20,66 +20,16 @@
 #include <tuple>
 #include <vector>
 
-#include "../../include/ietidp.h"
-#include "kernels.cuh"
+#include "host_internal.h"
+#include "engine.h"
+
+namespace ieti_host {
+thread_local std::string g_err;
+std::atomic<long long> g_kernel_launches{0};
+}  // namespace ieti_host
+using namespace ieti_host;
 
 namespace {
-
-thread_local std::string g_err;
-
-int fail(int code, const std::string& msg) {
-    g_err = msg;
-    return code;
-}
-
-#define CU(x)                                                                        \
-    do {                                                                             \
-        cudaError_t e_ = (x);                                                        \
-        if (e_ != cudaSuccess)                                                       \
-            return fail(e_ == cudaErrorMemoryAllocation ? IETIDP_E_OOM : IETIDP_E_CUDA, \
-                        std::string(#x) + ": " + cudaGetErrorString(e_));            \
-    } while (0)
-
-#define CHK(x)                         \
-    do {                               \
-        int rc_ = (x);                 \
-        if (rc_ != IETIDP_OK) return rc_; \
-    } while (0)
-
-// Device allocations of one owner, stream-ordered (cudaMallocAsync /
-// cudaFreeAsync on the owner's stream), so that releasing one problem's memory
-// never synchronizes work that other streams have in flight.
-struct DevMem {
-    cudaStream_t st = nullptr;
-    std::vector<void*> ptrs;
-    long long bytes = 0;
-    template <class T>
-    int alloc(T** p, long long n) {
-        *p = nullptr;
-        if (n <= 0) n = 1;
-        void* q = nullptr;
-        cudaError_t e = cudaMallocAsync(&q, sizeof(T) * (size_t)n, st);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            return fail(IETIDP_E_OOM, std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
-        }
-        ptrs.push_back(q);
-        bytes += (long long)sizeof(T) * n;
-        *p = (T*)q;
-        return IETIDP_OK;
-    }
-    template <class T>
-    int upload(T** p, const std::vector<T>& v, cudaStream_t s) {
-        CHK(alloc(p, (long long)v.size()));
-        if (!v.empty()) CU(cudaMemcpyAsync(*p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, s));
-        return IETIDP_OK;
-    }
-    void release() {
-        for (void* p : ptrs) cudaFreeAsync(p, st);
-        ptrs.clear();
-        bytes = 0;
-    }
-};
 
 struct UF {
     std::vector<long long> par;
@@ -101,99 +51,9 @@ struct UF {
 }  // namespace
 
 // ---------------------------------------------------------------------------
-struct iga_problem {
-    int dim = 0, npatch = 0;
-    std::vector<iga_patch_desc> patches;
-    std::vector<int> m;          // npatch*3 functions per direction
-    std::vector<int> dmask;
-    std::vector<long long> toff; // npatch+1
-    long long ntorn = 0;
-    // conforming identification: class id per torn index (-1 = patch-interior)
-    std::vector<long long> cls;      // per torn index: class id or -1
-    std::vector<std::vector<long long>> classes;   // torn indices of each class (sorted)
-    std::vector<char> cls_dir;       // class on the Dirichlet boundary
-    cudaStream_t stream = nullptr;
-    DevMem mem;
-    double* K64 = nullptr;           // fine stiffness (per patch, color-major)
-    std::vector<long long> koff;     // per patch offset in K64
-    std::vector<int> Sp;             // per patch padded row length
-    double* f = nullptr;             // load (torn)
-};
-
-struct SlotGroup {        // slots served by one kernel specialisation
-    int dim, p0, p1, p2;
-    bool generic = false;     // run-time-degree kernel (no specialisation)
-    bool xg = false;          // specialised kernel with V-cycle vectors in global memory
-    SlotDesc* d = nullptr;
-    int n = 0;
-    int its_off = 0;
-    size_t smem = 0;
-};
-
-constexpr size_t kSmemCap = kSolveSmemCap;   // dynamic shared memory per CTA
-
-struct ietidp_handle {
-    const iga_problem* prob = nullptr;
-    ietidp_options opt;
-    cudaStream_t st = nullptr;
-    DevMem mem;
-    int npatch = 0, dim = 0;
-    std::vector<PatchDesc> pd;
-    PatchDesc* d_pd = nullptr;
-    double* K64 = nullptr;
-    float* K32 = nullptr;
-    double* KM64 = nullptr;   // K + alpha M^ on floating patches (same offsets as K64)
-    float* KM32 = nullptr;
-    double* tab = nullptr;
-    float* tabf = nullptr;
-    int* itab = nullptr;
-    double* A0inv64 = nullptr;
-    float* A0inv32 = nullptr;
-    // constraints
-    int nrows = 0, npi = 0;
-    int *crow_ptr = nullptr, *c_idx = nullptr, *crow_patch = nullptr, *crow_local = nullptr,
-        *crow_glob = nullptr, *gptr = nullptr, *glist = nullptr;
-    double* c_w = nullptr;
-    double* phi = nullptr;
-    double* Linv = nullptr;
-    std::vector<double> spp_host;
-    double *rloc = nullptr, *upi = nullptr, *uloc = nullptr;
-    // dual
-    DualArgs dual{};
-    int nlam = 0;
-    // slots
-    std::vector<SlotGroup> gpatch;       // one slot per patch (Neumann / Schur)
-    std::vector<SlotGroup> gbasis;       // one slot per primal row
-    std::vector<cudaStream_t> side;
-    std::vector<cudaEvent_t> join;
-    cudaEvent_t fork = nullptr;
-    double* cg = nullptr;
-    void* lv = nullptr;
-    int* its = nullptr;
-    int* flags = nullptr;
-    int* dbg = nullptr;       // self-check record of debug builds (6 ints)
-    long long* phase = nullptr;   // phase timers of profiling builds (64)
-    long long* vst = nullptr;     // [0..4] Neumann-type stats, [8..12] basis stats
-    // torn buffers
-    double *gF = nullptr, *uF = nullptr, *vS = nullptr, *wS = nullptr, *gR = nullptr, *tmp = nullptr;
-    double *fH = nullptr, *uH = nullptr;   // device staging of ietidp_solve_host
-    // dual vectors
-    double *lam = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr, *d = nullptr;
-    double *state = nullptr, *hist = nullptr, *scal = nullptr;
-    double* h_pinned = nullptr;
-    double t_setup_ms = 0;
-    long long launches = 0;         // kernels launched since the last reset
-    std::vector<cudaEvent_t> ev;    // Neumann solver launch brackets (pairs)
-    int nev_used = 0;
-    double basis_it_avg = 0;
-    int basis_it_max = 0;
-    int n_floating = 0;
-    int device = 0;                 // device current at setup
-    long long cg_patch_elems = 0;   // FP64 scratch used by the per-patch slots
-    long long lv_patch_elems = 0;   // level-vector scratch used by the per-patch slots
-};
-
 extern "C" const char* ietidp_last_error(void) { return g_err.c_str(); }
+
+extern "C" long long ietidp_kernel_launches(void) { return g_kernel_launches.load(); }
 
 // set the calling thread's error text (used by the server to hand a worker's
 // error to the thread that polls the request)
@@ -524,18 +384,19 @@ static std::vector<std::array<int, 3>> schedule(const int* nel, int d, int cmin)
 static int launch_group(ietidp_handle* h, SolveArgs a, const SlotGroup& g, cudaStream_t st) {
     a.slots = g.d;
     a.nslots = g.n;
-    a.its = h->its + g.its_off;
+    a.its = h->its;
     a.smem_bytes = g.smem;
     cudaError_t e;
     if (!g.generic) e = launch_solve_variant(a, g.dim, g.p0, g.p1, g.p2, 512, st, g.xg);
     else e = launch_solve(a, 512, st);
     h->launches += 1;
+    g_kernel_launches += 1;
     if (e != cudaSuccess) return fail(IETIDP_E_CUDA, std::string("solve kernel: ") + cudaGetErrorString(e));
     return IETIDP_OK;
 }
 
-static int run_solve(ietidp_handle* h, int mode, const std::vector<SlotGroup>& groups, const double* in,
-                     double* out, double tol, int maxit, long long* vst) {
+SolveArgs ieti_solve_args(const ietidp_handle* h, int mode, const double* in, double* out, double tol, int maxit,
+                          long long* vst) {
     SolveArgs a{};
     a.pd = h->d_pd;
     a.mode = mode;
@@ -559,6 +420,7 @@ static int run_solve(ietidp_handle* h, int mode, const std::vector<SlotGroup>& g
     a.out = out;
     a.rpi_loc = h->rloc;
     a.upi_loc = h->uloc;
+    a.its = h->its;
     a.flags = h->flags;
     a.tol = tol;
     a.maxit = maxit;
@@ -569,6 +431,13 @@ static int run_solve(ietidp_handle* h, int mode, const std::vector<SlotGroup>& g
     a.vstats = vst;
     a.dbg = h->dbg;
     a.phase = h->phase;
+    a.batch = nullptr;
+    return a;
+}
+
+static int run_solve(ietidp_handle* h, int mode, const std::vector<SlotGroup>& groups, const double* in,
+                     double* out, double tol, int maxit, long long* vst) {
+    SolveArgs a = ieti_solve_args(h, mode, in, out, tol, maxit, vst);
     bool timed = mode == MODE_NEUMANN && h->nev_used + 2 <= (int)h->ev.size();
     if (timed) cudaEventRecord(h->ev[h->nev_used], h->st);
     if (groups.size() == 1) {
@@ -621,6 +490,7 @@ static int make_groups(ietidp_handle* h, const std::vector<SlotDesc>& slots, std
         g.n = (int)kv.second.size();
         g.its_off = off;
         off += g.n;
+        g.hs = kv.second;
         size_t need = 0;
         for (const SlotDesc& sd : kv.second) need = std::max(need, solve_smem_need(h->pd[sd.patch], mixed, g.xg));
         g.smem = std::min(need, kSmemCap);
@@ -1051,10 +921,10 @@ extern "C" int ietidp_setup(const iga_problem* P, const ietidp_options* opt_in, 
             cg_total += 5 * n;
             lv_total += nl;
         }
-        for (int k = 0; k < N; ++k) sp[k] = SlotDesc{k, 0, 0, 0, cgo[k], lvo[k]};
+        for (int k = 0; k < N; ++k) sp[k] = SlotDesc{k, 0, 0, k, 0, 0, cgo[k], lvo[k]};
         h->cg_patch_elems = N < nslots_max ? cgo[N] : cg_total;
         h->lv_patch_elems = N < nslots_max ? lvo[N] : lv_total;
-        for (int s = 0; s < nslot_basis; ++s) sb[s] = SlotDesc{crow_patch[s], 0, s, 0, cgo[s], lvo[s]};
+        for (int s = 0; s < nslot_basis; ++s) sb[s] = SlotDesc{crow_patch[s], 0, s, s, 0, 0, cgo[s], lvo[s]};
     }
     CKH(h->mem.alloc(&h->cg, cg_total));
     if (mixed) {
@@ -1182,6 +1052,7 @@ extern "C" int ietidp_setup(const iga_problem* P, const ietidp_options* opt_in, 
 static int ktilde_inv(ietidp_handle* h, const double* g, double* u) {
     cudaStream_t st = h->st;
     h->launches += (h->nrows > 0) + (h->npi > 0);
+    g_kernel_launches += (h->nrows > 0) + (h->npi > 0);
     cudaError_t e = launch_primal_restrict(h->d_pd, h->nrows, h->crow_patch, h->crow_local, h->phi, g, h->rloc, st);
     if (e == cudaSuccess)
         e = launch_coarse_solve(h->npi, h->nrows, h->crow_glob, h->gptr, h->glist, h->Linv, h->rloc, h->upi, h->uloc, st);
@@ -1191,6 +1062,7 @@ static int ktilde_inv(ietidp_handle* h, const double* g, double* u) {
 
 static int apply_F(ietidp_handle* h, const double* pv, double* qv) {
     h->launches += 2;
+    g_kernel_launches += 2;
     cudaError_t e = launch_bt(h->dual, pv, h->gF, 0, h->st);
     if (e != cudaSuccess) return fail(IETIDP_E_CUDA, cudaGetErrorString(e));
     CHK(ktilde_inv(h, h->gF, h->uF));
@@ -1201,174 +1073,13 @@ static int apply_F(ietidp_handle* h, const double* pv, double* qv) {
 
 static int apply_M(ietidp_handle* h, const double* rv, double* zv) {
     h->launches += 2;
+    g_kernel_launches += 2;
     cudaError_t e = launch_bt(h->dual, rv, h->vS, 1, h->st);
     if (e != cudaSuccess) return fail(IETIDP_E_CUDA, cudaGetErrorString(e));
     CHK(run_solve(h, MODE_SCHUR, h->gpatch, h->vS, h->wS, 0.0, 0, h->vst));
     e = launch_b(h->dual, h->wS, zv, 1, h->st);
     if (e != cudaSuccess) return fail(IETIDP_E_CUDA, cudaGetErrorString(e));
     return IETIDP_OK;
-}
-
-static double lanczos_kappa(const std::vector<double>& al, const std::vector<double>& be) {
-    int n = (int)al.size();
-    if (n == 0) return 1.0;
-    // symmetric tridiagonal eigenvalues by bisection (Sturm sequences)
-    std::vector<double> dd(n), ee(n, 0.0);
-    for (int k = 0; k < n; ++k) {
-        dd[k] = 1.0 / al[k] + (k > 0 ? be[k - 1] / al[k - 1] : 0.0);
-        if (k < n - 1 && k < (int)be.size()) ee[k] = std::sqrt(std::max(0.0, be[k])) / al[k];
-    }
-    double lo = 1e300, hi = -1e300;
-    for (int k = 0; k < n; ++k) {
-        double rad = std::fabs(k > 0 ? ee[k - 1] : 0.0) + std::fabs(ee[k]);
-        lo = std::min(lo, dd[k] - rad);
-        hi = std::max(hi, dd[k] + rad);
-    }
-    auto count_below = [&](double x) {
-        int c = 0;
-        double q = 1.0;
-        for (int k = 0; k < n; ++k) {
-            double e2 = k > 0 ? ee[k - 1] * ee[k - 1] : 0.0;
-            q = dd[k] - x - (k > 0 ? e2 / q : 0.0);
-            if (q == 0.0) q = -1e-300;
-            if (q < 0) ++c;
-        }
-        return c;
-    };
-    auto eig = [&](int idx) {
-        double a = lo, b = hi;
-        for (int it = 0; it < 200; ++it) {
-            double mid = 0.5 * (a + b);
-            if (count_below(mid) > idx) b = mid;
-            else a = mid;
-        }
-        return 0.5 * (a + b);
-    };
-    double emin = eig(0), emax = eig(n - 1);
-    return emax / emin;
-}
-
-static int read_flags(ietidp_handle* h, int* fl) {
-    CU(cudaMemcpyAsync(h->h_pinned + 8, h->flags, sizeof(int), cudaMemcpyDeviceToHost, h->st));
-    CU(cudaStreamSynchronize(h->st));
-    std::memcpy(fl, h->h_pinned + 8, sizeof(int));
-    return IETIDP_OK;
-}
-
-extern "C" int ietidp_solve(ietidp_handle* h, const double* f, double* u_out, ietidp_stats* stats) {
-    if (!h || !u_out) return fail(IETIDP_E_INVALID_ARG, "null argument");
-    auto t0 = std::chrono::steady_clock::now();
-    cudaStream_t st = h->st;
-    const iga_problem* P = h->prob;
-    if (!f) f = P->f;
-    CU(cudaMemsetAsync(h->flags, 0, sizeof(int), st));
-    CU(cudaMemsetAsync(h->vst, 0, sizeof(long long) * 8, st));
-    ietidp_stats S;
-    std::memset(&S, 0, sizeof(S));
-    h->launches = 0;
-    h->nev_used = 0;
-    // u0 = K~^{-1} f
-    CHK(ktilde_inv(h, f, u_out));
-    int it = 0;
-    bool conv = true;
-    std::vector<double> al, be;
-    if (h->nlam > 0) {
-        cudaError_t e = launch_b(h->dual, u_out, h->d, 0, st);
-        if (e == cudaSuccess) e = launch_jump_scale(h->dual, u_out, h->scal, st);
-        if (e == cudaSuccess) e = launch_outer_init(h->nlam, h->d, h->lam, h->r, h->state, st);
-        h->launches += 3;
-        if (e != cudaSuccess) return fail(IETIDP_E_CUDA, cudaGetErrorString(e));
-        CU(cudaMemcpyAsync(h->h_pinned, h->state + 5, sizeof(double), cudaMemcpyDeviceToHost, st));
-        CU(cudaMemcpyAsync(h->h_pinned + 1, h->scal, sizeof(double), cudaMemcpyDeviceToHost, st));
-        CU(cudaStreamSynchronize(st));
-        double dd = h->h_pinned[0], sc2 = h->h_pinned[1];
-        if (!std::isfinite(dd)) return fail(IETIDP_E_NONFINITE, "non-finite dual right-hand side");
-        S.d_norm = std::sqrt(dd);
-        S.d_scale = std::sqrt(sc2);
-        double tol = h->opt.tol_outer;
-        if (S.d_norm > tol * S.d_scale) {
-            conv = false;
-            CHK(apply_M(h, h->r, h->z));
-            e = launch_outer_first(h->nlam, h->r, h->z, h->p, h->state, st);
-            h->launches += 1;
-            if (e != cudaSuccess) return fail(IETIDP_E_CUDA, cudaGetErrorString(e));
-            double thr2 = tol * tol * dd;
-            for (it = 1; it <= h->opt.maxit_outer; ++it) {
-                CHK(apply_F(h, h->p, h->q));
-                e = launch_outer_step1(h->nlam, h->p, h->q, h->lam, h->r, h->state, h->hist, it - 1, st);
-                h->launches += 1;
-                if (e != cudaSuccess) return fail(IETIDP_E_CUDA, cudaGetErrorString(e));
-                CU(cudaMemcpyAsync(h->h_pinned, h->state + 4, sizeof(double), cudaMemcpyDeviceToHost, st));
-                CU(cudaStreamSynchronize(st));
-                double rr = h->h_pinned[0];
-                if (!std::isfinite(rr)) return fail(IETIDP_E_NONFINITE, "non-finite dual residual");
-                S.rel_res = std::sqrt(rr / dd);
-                if (rr <= thr2) {
-                    conv = true;
-                    break;
-                }
-                CHK(apply_M(h, h->r, h->z));
-                e = launch_outer_step2(h->nlam, h->r, h->z, h->p, h->state, h->hist, it - 1, st);
-                h->launches += 1;
-                if (e != cudaSuccess) return fail(IETIDP_E_CUDA, cudaGetErrorString(e));
-            }
-            if (!conv) it = h->opt.maxit_outer;
-            std::vector<double> hist(2 * (it + 1));
-            CU(cudaMemcpyAsync(hist.data(), h->hist, sizeof(double) * 2 * it, cudaMemcpyDeviceToHost, st));
-            CU(cudaStreamSynchronize(st));
-            for (int k = 0; k < it; ++k) {
-                al.push_back(hist[2 * k]);
-                if (k < it - 1) be.push_back(hist[2 * k + 1]);
-            }
-            // recovery: u = K~^{-1}(f - B^T lambda)
-            e = launch_bt(h->dual, h->lam, h->tmp, 0, st);
-            if (e == cudaSuccess) e = launch_axpy_torn(P->ntorn, f, -1.0, h->tmp, h->gR, st);
-            h->launches += 2;
-            if (e != cudaSuccess) return fail(IETIDP_E_CUDA, cudaGetErrorString(e));
-            CHK(ktilde_inv(h, h->gR, u_out));
-        }
-    }
-    int fl = 0;
-    CHK(read_flags(h, &fl));
-    long long vs[8];
-    CU(cudaMemcpy(vs, h->vst, sizeof(vs), cudaMemcpyDeviceToHost));
-    auto t1 = std::chrono::steady_clock::now();
-    S.outer_it = it;
-    S.converged = conv && !(fl & IETI_FLAG_NOT_CONVERGED);
-    S.kappa = lanczos_kappa(al, be);
-    S.vcycles = vs[0];
-    S.vcycle_dofs = vs[1];
-    S.basis_it_avg = h->basis_it_avg;
-    S.basis_it_max = h->basis_it_max;
-    S.t_setup_ms = h->t_setup_ms;
-    S.t_solve_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
-    S.launches = h->launches;
-    S.neumann_launches = h->nev_used / 2;
-    for (int k = 0; k + 1 < h->nev_used; k += 2) {
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, h->ev[k], h->ev[k + 1]);
-        S.neumann_ms += ms;
-    }
-    S.inner_its = vs[2];
-    if (vs[4] > 0) {
-        S.inner_it_avg = (double)vs[2] / (double)vs[4];
-        S.inner_it_max = (int)vs[3];
-    }
-    if (stats) *stats = S;
-    if (fl & IETI_FLAG_BREAKDOWN) return fail(IETIDP_E_BREAKDOWN, "CG breakdown in a local solve");
-    if (!S.converged) return fail(IETIDP_E_NOT_CONVERGED, "solver did not converge");
-    return IETIDP_OK;
-}
-
-extern "C" int ietidp_solve_host(ietidp_handle* h, const double* f_host, double* u_host, ietidp_stats* stats) {
-    if (!h || !u_host) return fail(IETIDP_E_INVALID_ARG, "null argument");
-    long long nt = h->prob->ntorn;
-    if (f_host) CU(cudaMemcpyAsync(h->fH, f_host, sizeof(double) * nt, cudaMemcpyHostToDevice, h->st));
-    int rc = ietidp_solve(h, f_host ? h->fH : nullptr, h->uH, stats);
-    if (rc != IETIDP_OK && rc != IETIDP_E_NOT_CONVERGED) return rc;
-    CU(cudaMemcpyAsync(u_host, h->uH, sizeof(double) * nt, cudaMemcpyDeviceToHost, h->st));
-    CU(cudaStreamSynchronize(h->st));
-    return rc;
 }
 
 extern "C" int ietidp_info_get(const ietidp_handle* h, ietidp_info* info) {
@@ -1459,6 +1170,8 @@ extern "C" int ietidp_get_spp(ietidp_handle* h, double* spp) {
 extern "C" int ietidp_destroy(ietidp_handle* h) {
     if (!h) return IETIDP_OK;
     cudaStreamSynchronize(h->st);
+    ieti_engine_destroy(h->engine);
+    h->engine = nullptr;
     h->mem.release();
     cudaStreamSynchronize(h->st);
     if (h->h_pinned) cudaFreeHost(h->h_pinned);

@@ -70,6 +70,8 @@ struct SlotDesc {
     int patch;
     int kind;            // 0: Neumann hierarchy, 1: Dirichlet hierarchy
     int row;             // basis mode: global C row
+    int its;             // index of the slot's iteration count in SolveArgs::its
+    int handle;          // batched launches: index of the slot's arguments in SolveArgs::batch
     int pad;
     long long cg;        // offset of the slot's FP64 vectors (5 n)
     long long lv;        // offset of the slot's level vectors (3 nlvec)
@@ -113,6 +115,10 @@ struct SolveArgs {
     size_t smem_bytes;         // dynamic shared memory of the launch (specialised kernels)
     int* dbg;                  // self-check record (debug builds only)
     long long* phase;          // phase timers (profiling builds only)
+    // batched launches (several handles in one grid): per-handle arguments,
+    // indexed by SlotDesc::handle; slots, nslots and smem_bytes of the launch
+    // itself stay those of this struct.  nullptr: a single handle.
+    const SolveArgs* batch;
 };
 
 // generic kernel (degrees known at run time only)
@@ -123,10 +129,14 @@ bool solve_variant_exists(int dim, int p0, int p1, int p2, int mixed);
 // shared-memory budget)
 cudaError_t launch_solve_variant(const SolveArgs& a, int dim, int p0, int p1, int p2, int threads,
                                  cudaStream_t st, bool xg);
+// resident CTAs per SM of a specialised launch (0 if no such kernel)
+int solve_variant_ctas_per_sm(int dim, int p0, int p1, int p2, int mixed, bool xg, int threads, size_t smem);
 // shared memory a specialised launch would use for this patch (uncapped)
 size_t solve_smem_need(const PatchDesc& P, int mixed, bool xg = false);
 // shared memory below which the specialised kernel cannot run this patch
 size_t solve_smem_min(const PatchDesc& P, int mixed);
+// shared memory of the per-level color tables alone (global-memory-vector variant's minimum)
+size_t solve_smem_tables(const PatchDesc& P);
 
 // ---- dual / primal helpers ---------------------------------------------------
 struct DualArgs {

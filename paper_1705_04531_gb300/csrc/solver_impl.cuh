@@ -625,12 +625,21 @@ __device__ inline void apply_C(const SolveArgs& a, const PatchDesc& P, const dou
 }
 
 template <typename T, int D, int P0, int P1, int P2, bool XG>
-__global__ void __launch_bounds__(512) k_solve_t(SolveArgs a) {
+__global__ void __launch_bounds__(512) k_solve_t(SolveArgs a0) {
     __shared__ Red red;
     __shared__ double coef[kMaxRows];
     __shared__ PatchDesc sP;
+    __shared__ SolveArgs sa;
     unsigned char* dyn = ieti_dyn;
-    const SlotDesc sd = a.slots[blockIdx.x];
+    const SlotDesc sd = a0.slots[blockIdx.x];
+    if (threadIdx.x == 0) {
+        sa = a0.batch ? a0.batch[sd.handle] : a0;
+        sa.slots = a0.slots;
+        sa.nslots = a0.nslots;
+        sa.smem_bytes = a0.smem_bytes;
+    }
+    __syncthreads();
+    const SolveArgs& a = sa;
 #ifdef IETI_DEBUG_BOUNDS
     if (threadIdx.x == 0) g_ieti_dbg = a.dbg;
     __syncthreads();
@@ -854,7 +863,7 @@ __global__ void __launch_bounds__(512) k_solve_t(SolveArgs a) {
         if (!conv && it > a.maxit) it = a.maxit;
     }
     if (threadIdx.x == 0) {
-        a.its[blockIdx.x] = it;
+        a.its[sd.its] = it;
         if (!conv) atomicOr(a.flags, IETI_FLAG_NOT_CONVERGED);
         if (a.vstats) {
             atomicAdd((unsigned long long*)&a.vstats[0], (unsigned long long)vcount);
@@ -880,15 +889,18 @@ __global__ void __launch_bounds__(512) k_solve_t(SolveArgs a) {
     }
 }
 
+// occ != nullptr: report the resident CTAs per SM of a launch with `threads`
+// threads and a.smem_bytes dynamic shared memory instead of launching
 template <typename T, int D, int P0, int P1, int P2, bool XG>
-cudaError_t launch_t(const SolveArgs& a, int threads, cudaStream_t st) {
-    if (a.nslots == 0) return cudaSuccess;
+cudaError_t launch_t(const SolveArgs& a, int threads, cudaStream_t st, int* occ) {
     auto kern = k_solve_t<T, D, P0, P1, P2, XG>;
     // the attribute is an upper bound shared by all host threads: always set
     // the fixed cap (a smaller value set by one thread could otherwise race
     // with a larger launch from another)
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSolveSmemCap);
     if (e != cudaSuccess) return e;
+    if (occ) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, kern, threads, a.smem_bytes);
+    if (a.nslots == 0) return cudaSuccess;
     kern<<<a.nslots, threads, a.smem_bytes, st>>>(a);
     return cudaGetLastError();
 }

@@ -378,10 +378,19 @@ __device__ void apply_C(const SolveArgs& a, const PatchDesc& P, const double* v,
 }
 
 template <typename T>
-__global__ void __launch_bounds__(512) k_solve(SolveArgs a) {
+__global__ void __launch_bounds__(512) k_solve(SolveArgs a0) {
     __shared__ Red red;
     __shared__ double coef[kMaxRows];
-    const SlotDesc sd = a.slots[blockIdx.x];
+    __shared__ SolveArgs sa;
+    const SlotDesc sd = a0.slots[blockIdx.x];
+    if (threadIdx.x == 0) {
+        sa = a0.batch ? a0.batch[sd.handle] : a0;
+        sa.slots = a0.slots;
+        sa.nslots = a0.nslots;
+        sa.smem_bytes = a0.smem_bytes;
+    }
+    __syncthreads();
+    const SolveArgs& a = sa;
     const PatchDesc& P = a.pd[sd.patch];
     const LevelDesc& F = P.lev[P.L - 1];
     const int n = F.n;
@@ -588,7 +597,7 @@ __global__ void __launch_bounds__(512) k_solve(SolveArgs a) {
         if (!conv && it > a.maxit) it = a.maxit;
     }
     if (threadIdx.x == 0) {
-        a.its[blockIdx.x] = it;
+        a.its[sd.its] = it;
         if (!conv) atomicOr(a.flags, IETI_FLAG_NOT_CONVERGED);
         if (a.vstats) {
             atomicAdd((unsigned long long*)&a.vstats[0], (unsigned long long)vcount);

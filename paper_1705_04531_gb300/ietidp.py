@@ -91,6 +91,10 @@ _SIGS = {
     "ietidp_patch_offsets": (C.c_int, [_vp, C.POINTER(C.c_longlong)]),
     "ietidp_solve": (C.c_int, [_vp, _vp, _vp, C.POINTER(ietidp_stats)]),
     "ietidp_solve_host": (C.c_int, [_vp, _vp, _vp, C.POINTER(ietidp_stats)]),
+    "ietidp_solve_batch": (C.c_int, [_vp, C.c_int, _vp, _vp, C.POINTER(ietidp_stats)]),
+    "ietidp_solve_batch_host": (C.c_int, [_vp, C.c_int, _vp, _vp, C.POINTER(ietidp_stats)]),
+    "ietidp_autotune_table": (C.c_int, [_vp, C.c_int]),
+    "ietidp_kernel_launches": (C.c_longlong, []),
     "ietidp_vcycles": (C.c_int, [_vp, _vp, _vp, C.c_int]),
     "ietidp_vcycles_noalloc": (C.c_int, [_vp, _vp, _vp, C.c_int]),
     "ietidp_apply_K": (C.c_int, [_vp, _vp, _vp]),
@@ -237,6 +241,43 @@ def ietidp_solve_host(handle, f_host, u_host):
     return st.as_dict()
 
 
+def ietidp_solve_batch(handles, fs, us):
+    """Lockstep solve of several handles (device vectors; fs entries may be
+    None for the assembled load).  Returns one stats dict per handle."""
+    n = len(handles)
+    hs = (C.c_void_p * n)(*[h.value if isinstance(h, C.c_void_p) else h for h in handles])
+    fp = (C.c_void_p * n)(*[None if f is None else f.data_ptr() for f in fs])
+    up = (C.c_void_p * n)(*[u.data_ptr() for u in us])
+    st = (ietidp_stats * n)()
+    _check(_lib.ietidp_solve_batch(hs, n, fp, up, st))
+    return [s.as_dict() for s in st]
+
+
+def ietidp_solve_batch_host(handles, fs, us):
+    """Same as ietidp_solve_batch with host numpy arrays (fs entries may be None)."""
+    n = len(handles)
+    hs = (C.c_void_p * n)(*[h.value if isinstance(h, C.c_void_p) else h for h in handles])
+    fp = (C.c_void_p * n)(*[None if f is None else f.ctypes.data for f in fs])
+    up = (C.c_void_p * n)(*[u.ctypes.data for u in us])
+    st = (ietidp_stats * n)()
+    _check(_lib.ietidp_solve_batch_host(hs, n, fp, up, st))
+    return [s.as_dict() for s in st]
+
+
+def kernel_launches():
+    """Kernels the library's solve entry points launched in this process."""
+    return int(_lib.ietidp_kernel_launches())
+
+
+def autotune_table():
+    """Autotuner decisions: list of dicts (shape key and chosen configuration)."""
+    n = _lib.ietidp_autotune_table(None, 0)
+    buf = (C.c_int * (10 * max(n, 1)))()
+    n = _lib.ietidp_autotune_table(buf, n)
+    keys = ("dim", "p0", "p1", "p2", "kind", "mixed", "waves", "threads", "smem", "ctas_per_sm")
+    return [dict(zip(keys, buf[10 * i:10 * i + 10])) for i in range(n)]
+
+
 class Problem:
     """An assembled multipatch problem (device resident)."""
 
@@ -294,6 +335,27 @@ class Solver:
             u_host = np.empty(self.n_torn)
         st = ietidp_solve_host(self.h, f_host, u_host)
         return u_host, st
+
+    @staticmethod
+    def solve_batch(solvers, fs=None, us=None):
+        """Solve every solver's problem in one lockstep batch (device tensors)."""
+        import torch
+        if fs is None:
+            fs = [None] * len(solvers)
+        if us is None:
+            us = [torch.empty(s.n_torn, dtype=torch.float64, device="cuda") for s in solvers]
+        st = ietidp_solve_batch([s.h for s in solvers], fs, us)
+        return us, st
+
+    @staticmethod
+    def solve_batch_host(solvers, fs=None, us=None):
+        """Batched solve with host numpy buffers."""
+        if fs is None:
+            fs = [None] * len(solvers)
+        if us is None:
+            us = [np.empty(s.n_torn) for s in solvers]
+        st = ietidp_solve_batch_host([s.h for s in solvers], fs, us)
+        return us, st
 
     def vcycles(self, b, x, ncycles):
         _check(_lib.ietidp_vcycles(self.h, _ptr(b), _ptr(x), int(ncycles)))
