@@ -282,17 +282,18 @@ int ietidp_phase_timers(ietidp_handle* h, long long* out64);
 int ietidp_destroy(ietidp_handle* h);
 
 /* ---- continuous-batching server ---------------------------------------
- * Requests are queued as they arrive; a pool of `max_concurrent` worker
- * threads, each with its own CUDA stream, admits queued requests while the
- * estimated device memory of all admitted requests stays within
- * `budget_bytes` (first come first served; a request that does not fit lets
- * later smaller ones pass).  An admitted request runs iga_assemble_patches,
- * ietidp_setup and the solve on its worker's stream, so the kernels of all
- * admitted requests overlap on the device; its data stays resident until its
- * solution is on the host.  The domain descriptor is copied at submission,
- * except quad_values (device, must stay valid until the request is done).
- * Each request's result is independent of what else runs (same kernels, same
- * order of operations on its own buffers). */
+ * Requests are queued as they arrive.  `max_concurrent` setup workers, each
+ * with its own CUDA stream, admit queued requests while the estimated device
+ * memory of all admitted requests stays within `budget_bytes` (first come
+ * first served; a request that does not fit lets later smaller ones pass) and
+ * run iga_assemble_patches and ietidp_setup.  Set-up requests join one solve
+ * loop between outer iterations: the local solves of all requests in flight
+ * run in shared merged launches (ietidp_solve_batch), and a request leaves
+ * when it has converged.  Its data stays resident until its solution is on
+ * the host.  The domain descriptor is copied at submission, except
+ * quad_values (device, must stay valid until the request is done).  A
+ * request's result does not depend on what else runs, up to the rounding of
+ * dot products under another autotuned block size. */
 typedef struct ietidp_server ietidp_server;
 int ietidp_server_create(long long budget_bytes, int max_concurrent, const ietidp_options* opt,
                          ietidp_server** out);

@@ -1,15 +1,17 @@
 // Continuous-batching solve server.
 //
 // Requests (multipatch Poisson problems of any size) are queued as they
-// arrive.  A pool of worker threads, each owning one non-blocking CUDA stream,
-// admits queued requests while the estimated device memory of the admitted
-// requests stays within the budget (first come first served, a request that
-// does not fit lets later, smaller ones pass).  An admitted request runs
-// assembly, IETI-DP setup and the dual PCG solve on its worker's stream, so
-// the kernels of all admitted requests overlap on the device; its operator,
-// multigrid hierarchy, primal basis and multipliers stay resident until its
-// solution has been copied to the host, then its memory is returned to the
-// stream-ordered pool and the next request is admitted.
+// arrive.  Setup workers, each owning one non-blocking CUDA stream, admit
+// queued requests while the estimated device memory of the admitted requests
+// stays within the budget (first come first served; a request that does not
+// fit lets later, smaller ones pass) and run assembly and IETI-DP setup on
+// their stream.  A set-up request joins the solve loop's batch engine at the
+// next outer-iteration boundary: from then on its local solves share the
+// merged launches of every other request in flight, and it leaves the batch
+// when its dual PCG has converged.  Its operator, multigrid hierarchy, primal
+// basis and multipliers stay resident until its solution has been copied to
+// the host; then its memory returns to the stream-ordered pool and its budget
+// share to the admission queue.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -24,7 +26,7 @@
 #include <thread>
 #include <vector>
 
-#include "../../include/ietidp.h"
+#include "engine.h"
 
 void ieti_set_error(const std::string& msg);   // ietidp_host.cu
 
@@ -46,7 +48,10 @@ struct Request {
     const double* quad_values = nullptr;
     long long est_bytes = 0;
     long long ntorn = 0;
-    double t_submit = 0, t_start = 0, t_done = 0;
+    double t_submit = 0, t_start = 0, t_setup = 0, t_done = 0;
+    iga_problem* prob = nullptr;
+    ietidp_handle* h = nullptr;
+    double* h_u_dev = nullptr;   // the handle's device output buffer
     int state = 0;   // 0 queued, 1 running, 2 done
     int rc = 0;
     std::string err;
@@ -93,19 +98,42 @@ struct ietidp_server {
     ietidp_options opt{};
     std::mutex mu;
     std::condition_variable cv;
-    std::deque<unsigned long long> queue;
+    std::deque<unsigned long long> queue;                  // submitted, not admitted
     std::map<unsigned long long, std::shared_ptr<Request>> reqs;
+    std::deque<std::shared_ptr<Request>> ready;            // set up, waiting to join the solve batch
     long long in_flight = 0;
     int running = 0;
     bool stop = false;
     unsigned long long next_ticket = 1;
     std::vector<std::thread> workers;
+    std::thread solver;
     int device = 0;
     int completed = 0;
 
     void worker(int wid);
+    void solve_loop();
+    void release(const std::shared_ptr<Request>& r);
 };
 
+// a request leaves: its device memory goes back to the pool and the budget
+void ietidp_server::release(const std::shared_ptr<Request>& r) {
+    if (r->h) ietidp_destroy(r->h);
+    if (r->prob) iga_problem_free(r->prob);
+    r->h = nullptr;
+    r->prob = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        r->t_done = now_s();
+        r->state = 2;
+        in_flight -= r->est_bytes;
+        running -= 1;
+        completed += 1;
+    }
+    cv.notify_all();
+}
+
+// setup workers: admit by budget, assemble and set up on the worker's own
+// stream, then hand the request to the solve loop
 void ietidp_server::worker(int /*wid*/) {
     cudaSetDevice(device);
     cudaStream_t st;
@@ -138,7 +166,6 @@ void ietidp_server::worker(int /*wid*/) {
                 cv.wait(lk);
             }
         }
-        // ---- run the request on this worker's stream ----
         iga_domain_desc dd;
         std::memset(&dd, 0, sizeof(dd));
         dd.dim = r->dim;
@@ -152,32 +179,97 @@ void ietidp_server::worker(int /*wid*/) {
         dd.mode_k = r->mk.data();
         dd.mode_l = r->ml.data();
         dd.quad_values = r->quad_values;
-        iga_problem* prob = nullptr;
-        ietidp_handle* h = nullptr;
-        int rc = iga_assemble_patches(&dd, st, &prob);
-        if (rc == IETIDP_OK) rc = ietidp_setup(prob, &opt, st, &h);
+        int rc = iga_assemble_patches(&dd, st, &r->prob);
+        if (rc == IETIDP_OK) rc = ietidp_setup(r->prob, &opt, st, &r->h);
         if (rc == IETIDP_OK) {
             ietidp_info info;
-            ietidp_info_get(h, &info);
+            ietidp_info_get(r->h, &info);
             r->ntorn = info.n_torn;
             r->u.assign((size_t)info.n_torn, 0.0);
-            rc = ietidp_solve_host(h, nullptr, r->u.data(), &r->stats);
+            r->h_u_dev = r->h->uH;
+            if (cudaStreamSynchronize(st) != cudaSuccess) rc = IETIDP_E_CUDA;
         }
-        std::string err = rc == IETIDP_OK ? "" : ietidp_last_error();
-        if (h) ietidp_destroy(h);
-        if (prob) iga_problem_free(prob);
+        r->t_setup = now_s();
+        if (rc != IETIDP_OK) {
+            r->rc = rc;
+            r->err = ietidp_last_error();
+            release(r);
+            continue;
+        }
         {
             std::lock_guard<std::mutex> lk(mu);
-            r->rc = rc;
-            r->err = err;
-            r->t_done = now_s();
-            r->state = 2;
-            in_flight -= r->est_bytes;
-            running -= 1;
-            completed += 1;
+            ready.push_back(r);
         }
         cv.notify_all();
     }
+}
+
+// solve loop: one batch engine; requests join between outer iterations and
+// leave when converged, so the local solves of every admitted request share
+// the same launches
+void ietidp_server::solve_loop() {
+    cudaSetDevice(device);
+    cudaStream_t st;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return;
+    ieti_engine* E = nullptr;
+    if (ieti_engine_create(st, &E) != IETIDP_OK) {
+        cudaStreamDestroy(st);
+        return;
+    }
+    std::vector<std::shared_ptr<Request>> active;
+    std::vector<std::unique_ptr<EngineJob>> jobs;
+    for (;;) {
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            if (active.empty()) cv.wait(lk, [&] { return stop || !ready.empty(); });
+            if (stop && active.empty() && ready.empty()) break;
+            while (!ready.empty()) {
+                auto r = ready.front();
+                ready.pop_front();
+                auto j = std::make_unique<EngineJob>();
+                ieti_engine_job_init(*j, r->h, nullptr, r->h_u_dev);
+                active.push_back(r);
+                jobs.push_back(std::move(j));
+            }
+        }
+        std::vector<EngineJob*> ptr;
+        for (auto& j : jobs) ptr.push_back(j.get());
+        int rc = ieti_engine_tick(E, ptr);
+        std::string terr = rc == IETIDP_OK ? "" : ietidp_last_error();
+        // finished (or failed) requests: copy the solution out and release
+        std::vector<std::shared_ptr<Request>> keep_r;
+        std::vector<std::unique_ptr<EngineJob>> keep_j;
+        for (size_t i = 0; i < active.size(); ++i) {
+            auto& r = active[i];
+            EngineJob& j = *jobs[i];
+            if (rc != IETIDP_OK) {
+                j.rc = rc;
+                j.err = terr;
+                j.phase = EngineJob::DONE;
+            }
+            if (j.phase != EngineJob::DONE) {
+                keep_r.push_back(r);
+                keep_j.push_back(std::move(jobs[i]));
+                continue;
+            }
+            r->stats = j.S;
+            r->rc = j.rc;
+            r->err = j.err;
+            if (j.rc == IETIDP_OK || j.rc == IETIDP_E_NOT_CONVERGED) {
+                if (cudaMemcpyAsync(r->u.data(), r->h_u_dev, sizeof(double) * r->ntorn, cudaMemcpyDeviceToHost,
+                                    st) != cudaSuccess ||
+                    cudaStreamSynchronize(st) != cudaSuccess) {
+                    r->rc = IETIDP_E_CUDA;
+                    r->err = "copy of the solution to the host failed";
+                }
+            }
+            release(r);
+        }
+        active.swap(keep_r);
+        jobs.swap(keep_j);
+    }
+    ieti_engine_destroy(E);
+    cudaStreamDestroy(st);
 }
 
 extern "C" int ietidp_server_create(long long budget_bytes, int max_concurrent, const ietidp_options* opt,
@@ -190,6 +282,7 @@ extern "C" int ietidp_server_create(long long budget_bytes, int max_concurrent, 
     else ietidp_default_options(&s->opt);
     cudaGetDevice(&s->device);
     for (int i = 0; i < max_concurrent; ++i) s->workers.emplace_back([s, i] { s->worker(i); });
+    s->solver = std::thread([s] { s->solve_loop(); });
     *out = s;
     return IETIDP_OK;
 }
@@ -279,6 +372,7 @@ extern "C" int ietidp_server_destroy(ietidp_server* s) {
     }
     s->cv.notify_all();
     for (auto& w : s->workers) w.join();
+    s->solver.join();
     delete s;
     return IETIDP_OK;
 }
