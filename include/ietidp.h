@@ -121,6 +121,13 @@ typedef struct {
 typedef struct iga_problem   iga_problem;
 typedef struct ietidp_handle ietidp_handle;
 
+/* Outer method (Sec. 3.3): dual PCG on F lambda = d with accurate local
+ * Neumann solves (MG-MG), or Bramble-Pasciak CG on the saddle-point system
+ * of Eq. 2 with a fixed number of V-cycles in the preconditioner of K~
+ * (MG-MG-S). */
+#define IETIDP_METHOD_DUAL   0
+#define IETIDP_METHOD_SADDLE 1
+
 typedef struct {
     unsigned primal;          /* IETIDP_PRIMAL_* bitmask                       */
     int    precision;         /* IETIDP_PREC_*                                 */
@@ -133,7 +140,10 @@ typedef struct {
     int    coarse_elems;      /* coarsen while a direction has more elements (4) */
     int    dirichlet_vcycles; /* V-cycles for K_II^{-1} in the preconditioner (2) */
     double alpha_reg;         /* K_M = K + alpha M^ on floating patches (1e-2)  */
-    int    cluster;           /* CTAs per local problem (0 = autotune)         */
+    int    cluster;           /* reserved (0)                                  */
+    int    method;            /* IETIDP_METHOD_* (dual PCG, MG-MG)             */
+    int    saddle_vcycles;    /* MG-MG-S: V-cycles in the K~ preconditioner (3) */
+    double saddle_theta;      /* MG-MG-S: block scaling theta (0.9)            */
 } ietidp_options;
 
 typedef struct {

@@ -36,15 +36,17 @@ Reading (the paper does not state it): BPCG needs K~ - Khat positive
 definite, so each block of the preconditioner is scaled below its operator:
 the primal block by omega_Pi = theta, the Delta block of patch k by
 omega_k = theta (1 - rho_k^3), where rho_k estimates the energy-norm
-contraction of one V-cycle (20 power iterations of I - V K on the patch's
+contraction of one V-cycle (60 power iterations of I - V K on the patch's
 Neumann hierarchy operator, from the fixed start vector
 x_i = ((37 i) mod 101) / 101 - 1/2) and theta = 0.9.  Three V-cycles give
 P V3 P^T >= (1 - rho^3) times the exact Delta inverse, so
 Khat = omega (block preconditioner) stays below K~ (checked densely in the
 tests; a fixed omega = 0.9 fails for p = 3 on the annulus, where
-rho ~ 0.75).  The iteration stops when the preconditioned residual,
-measured in the BPCG inner product, has dropped by tol_outer relative to
-the first one; a non-positive inner product is a breakdown.
+rho ~ 0.75; with p = 4, rho ~ 0.9 and 20 power iterations underestimate
+it).  The iteration stops when the preconditioned residual, measured in the
+BPCG inner product, has dropped by tol_outer relative to the first one; a
+non-positive inner product after a step halves every scaling and restarts
+from the current iterate.
 
 BPCG with Schur preconditioner (Bramble-Pasciak transformation): with
 P_BP = [Khat 0; B~ -Shat], the matrix P_BP^{-1} [K~ B~^T; B~ 0] is
@@ -72,7 +74,7 @@ def power_start(n):
     return ((37 * i) % 101) / 101.0 - 0.5
 
 
-def vcycle_contraction(mg, its=20):
+def vcycle_contraction(mg, its=60):
     """Energy-norm contraction of one V-cycle, I - V A with A the hierarchy's
     fine operator, by power iteration (the last ratio)."""
     A = mg.A[-1]
@@ -90,7 +92,7 @@ def vcycle_contraction(mg, its=20):
 class SaddleOps:
     """The operators of Eq. 2 on V~ x Lambda for an IETIDP set up in mode "mg"."""
 
-    def __init__(self, s, theta=0.9, ncycles=3, power_its=20, omega=None):
+    def __init__(self, s, theta=0.9, ncycles=3, power_its=60, omega=None):
         if s.o.mode != "mg":
             raise ValueError("MG-MG-S needs the multigrid set-up (mode 'mg')")
         self.s = s
@@ -171,21 +173,33 @@ class SaddleOps:
         return self.restrict(self.s.f)
 
 
-def bpcg(s, tol=None, maxit=None, theta=0.9, ncycles=3):
-    """MG-MG-S solve.  Returns (u as full local tensor grids, stats dict)."""
-    ops = SaddleOps(s, theta, ncycles)
+def bpcg(s, tol=None, maxit=None, theta=0.9, ncycles=3, power_its=60):
+    """MG-MG-S solve.  Returns (u as full local tensor grids, stats dict).
+
+    Safeguard (part of the reading): a non-positive inner product after a
+    step means Khat is not below K~ (the contraction was underestimated);
+    every block scaling is then halved and the iteration restarts from the
+    current iterate with its residual recomputed."""
+    ops = SaddleOps(s, theta, ncycles, power_its)
     tol = s.o.tol_outer if tol is None else tol
     maxit = s.o.maxit_outer if maxit is None else maxit
     f = ops.rhs()
     x_u, x_l = ops.zeros_u(), np.zeros(s.nlam)
-    # unpreconditioned residual (b - [K~ B~^T; B~ 0] x) and preconditioned r
-    rt_u, rt_l = f, np.zeros(s.nlam)
-    r_u = ops.Khat_inv(rt_u)
-    Br = ops.B(r_u)
-    r_l = ops.Shat_inv(Br - rt_l)
+
+    def start(x_u, x_l):
+        # unpreconditioned residual (b - [K~ B~^T; B~ 0] x) and preconditioned r
+        rt_u = ops.axpy_u(ops.axpy_u(f, -1.0, ops.K(x_u)), -1.0, ops.BT(x_l))
+        rt_l = -ops.B(x_u)
+        r_u = ops.Khat_inv(rt_u)
+        Br = ops.B(r_u)
+        r_l = ops.Shat_inv(Br - rt_l)
+        return rt_u, rt_l, r_u, Br, r_l
+
+    rt_u, rt_l, r_u, Br, r_l = start(x_u, x_l)
     rho0 = None
     it = 0
     conv = False
+    restarts = 0
     p_u = p_l = Kp = KmKp = Sp = Bp = None
     rho_old = None
     hist = []
@@ -197,7 +211,14 @@ def bpcg(s, tol=None, maxit=None, theta=0.9, ncycles=3):
         if rho0 is None:
             rho0 = rho
         if rho < 0.0:
-            break                                   # the inner product is not definite
+            if p_u is None or restarts >= 10:
+                break                               # the inner product is not definite
+            ops.omega_pi *= 0.5
+            ops.omega = [w * 0.5 for w in ops.omega]
+            rt_u, rt_l, r_u, Br, r_l = start(x_u, x_l)
+            p_u = None
+            restarts += 1
+            continue
         hist.append(np.sqrt(rho / rho0) if rho0 > 0 else 0.0)
         if rho0 == 0.0 or rho <= tol * tol * rho0:
             conv = True
@@ -234,4 +255,4 @@ def bpcg(s, tol=None, maxit=None, theta=0.9, ncycles=3):
         it += 1
     u = s._expand(ops.function(x_u))
     return u, {"iterations": it, "converged": conv, "hist": hist, "lambda": x_l,
-               "rho": ops.rho, "omega": ops.omega}
+               "rho": ops.rho, "omega": ops.omega, "restarts": restarts}

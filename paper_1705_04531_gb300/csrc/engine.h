@@ -15,7 +15,9 @@ struct EngineJob {
     // INIT: u0 = K~^{-1} f next; PRECF / PREC: preconditioner (first / later
     // iteration) in this tick's stage B; ITER: F p next; RECOVER: recovery
     // solve next; DONE: result and stats final
-    enum Phase { INIT, PRECF, ITER, PREC, RECOVER, DONE };
+    // (MG-MG-S: RESTART recomputes the residual from the iterate; mixed-
+    // precision refinement)
+    enum Phase { INIT, PRECF, ITER, PREC, RECOVER, DONE, RESTART };
     ietidp_handle* h = nullptr;
     const double* f = nullptr;   // torn right-hand side (device)
     double* u = nullptr;         // torn solution (device)
@@ -29,6 +31,10 @@ struct EngineJob {
     std::chrono::steady_clock::time_point t0;
     int flags = 0;
     long long vs[8] = {};
+    double rho0 = 0.0;           // MG-MG-S: first BPCG inner product
+    double rho_cycle = 0.0;      // MG-MG-S: inner product at the last (re)start
+    bool fresh = false;          // MG-MG-S: next step starts a new search direction
+    int restarts = 0;
     std::vector<double> al, be;  // CG coefficients (Lanczos condition estimate)
 };
 
@@ -41,3 +47,15 @@ void ieti_engine_job_init(EngineJob& j, ietidp_handle* h, const double* f, doubl
 int ieti_engine_tick(ieti_engine* E, std::vector<EngineJob*>& jobs);
 // ticks until every job is DONE
 int ieti_engine_run(ieti_engine* E, std::vector<EngineJob*>& jobs);
+// one merged local-solve launch (stage 0 or 1 staging buffers: at most one
+// use of each per synchronisation interval); timed: bracket it with the
+// engine's events (ieti_engine_timed_ms after the next synchronisation)
+int ieti_engine_merged(ieti_engine* E, int stage, std::vector<std::pair<ietidp_handle*, SolveArgs>>& items,
+                       long long* nlaunch, bool timed);
+float ieti_engine_timed_ms(ieti_engine* E);
+// pinned read-back buffer of at least n doubles (valid until the next call)
+int ieti_engine_readback(ieti_engine* E, size_t n, double** out);
+// MG-MG-S jobs (handles with method IETIDP_METHOD_SADDLE), lockstep BPCG:
+// one iteration of every job (none DONE) / iterations until all are DONE
+int ieti_saddle_tick(ieti_engine* E, std::vector<EngineJob*>& jobs);
+int ieti_saddle_run(ieti_engine* E, std::vector<EngineJob*>& jobs);

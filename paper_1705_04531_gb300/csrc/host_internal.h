@@ -165,7 +165,11 @@ struct ietidp_handle {
     long long cg_patch_elems = 0;   // FP64 scratch used by the per-patch slots
     long long lv_patch_elems = 0;   // level-vector scratch used by the per-patch slots
     struct ieti_engine* engine = nullptr;   // solve engine on this handle's stream (created on first solve)
+    struct ieti_saddle_bufs* saddle = nullptr;   // MG-MG-S vectors (created on first saddle solve)
 };
+
+// release the host part of the MG-MG-S buffers (device memory is the handle's)
+void ieti_saddle_free(ietidp_handle* h);
 
 // kernel arguments of one handle for a local-solve launch (slots, nslots and
 // smem_bytes are filled by the caller)

@@ -672,6 +672,37 @@ int ieti_engine_tick(ieti_engine* E, std::vector<EngineJob*>& jobs) {
     return IETIDP_OK;
 }
 
+int ieti_engine_merged(ieti_engine* E, int stage, std::vector<std::pair<ietidp_handle*, SolveArgs>>& items,
+                       long long* nlaunch, bool timed) {
+    if (timed) CU(cudaEventRecord(E->e0, E->st));
+    CHK(merged_launch(E, stage == 0 ? E->stA : E->stB, items, nlaunch));
+    if (timed) CU(cudaEventRecord(E->e1, E->st));
+    return IETIDP_OK;
+}
+
+int ieti_engine_readback(ieti_engine* E, size_t n, double** out) {
+    if (n > E->cap_rb) {
+        CU(cudaStreamSynchronize(E->st));
+        if (E->h_rb) cudaFreeHost(E->h_rb);
+        E->h_rb = nullptr;
+        E->cap_rb = 0;
+        const size_t cap = std::max(n, (size_t)256);
+        CU(cudaMallocHost((void**)&E->h_rb, sizeof(double) * cap));
+        E->cap_rb = cap;
+    }
+    *out = E->h_rb;
+    return IETIDP_OK;
+}
+
+float ieti_engine_timed_ms(ieti_engine* E) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, E->e0, E->e1) != cudaSuccess) {
+        cudaGetLastError();
+        return 0.f;
+    }
+    return ms;
+}
+
 int ieti_engine_run(ieti_engine* E, std::vector<EngineJob*>& jobs) {
     for (;;) {
         bool any = false;
@@ -750,7 +781,12 @@ int run_jobs(ietidp_handle* const* hs, int n, std::vector<EngineJob>& jobs, bool
             }
     std::vector<EngineJob*> ptr;
     for (auto& j : jobs) ptr.push_back(&j);
-    int rc = ieti_engine_run(E, ptr);
+    const int method = hs[0]->opt.method;
+    int rc = IETIDP_OK;
+    for (int i = 1; i < n; ++i)
+        if (hs[i]->opt.method != method) rc = fail(IETIDP_E_INVALID_ARG, "a batch mixes outer methods");
+    if (rc == IETIDP_OK)
+        rc = method == IETIDP_METHOD_SADDLE ? ieti_saddle_run(E, ptr) : ieti_engine_run(E, ptr);
     if (rc == IETIDP_OK && host) {
         for (int i = 0; i < n; ++i) {
             if (jobs[i].rc != IETIDP_OK && jobs[i].rc != IETIDP_E_NOT_CONVERGED) continue;

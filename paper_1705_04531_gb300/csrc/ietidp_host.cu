@@ -74,6 +74,9 @@ extern "C" void ietidp_default_options(ietidp_options* o) {
     o->dirichlet_vcycles = 2;
     o->alpha_reg = 1e-2;
     o->cluster = 0;
+    o->method = IETIDP_METHOD_DUAL;
+    o->saddle_vcycles = 3;
+    o->saddle_theta = 0.9;
 }
 
 // ---------------------------------------------------------------------------
@@ -512,6 +515,9 @@ extern "C" int ietidp_setup(const iga_problem* P, const ietidp_options* opt_in, 
         opt.maxit_inner < 1 || opt.maxit_outer < 0 || !(opt.tol_outer > 0) || !(opt.tol_inner > 0) ||
         !(opt.tol_basis > 0) || opt.alpha_reg < 0)
         return fail(IETIDP_E_INVALID_ARG, "bad options");
+    if ((opt.method != IETIDP_METHOD_DUAL && opt.method != IETIDP_METHOD_SADDLE) || opt.saddle_vcycles < 1 ||
+        !(opt.saddle_theta > 0 && opt.saddle_theta < 1))
+        return fail(IETIDP_E_INVALID_ARG, "bad method options");
     auto t0 = std::chrono::steady_clock::now();
     auto* h = new ietidp_handle();
     h->prob = P;
@@ -1172,6 +1178,7 @@ extern "C" int ietidp_destroy(ietidp_handle* h) {
     cudaStreamSynchronize(h->st);
     ieti_engine_destroy(h->engine);
     h->engine = nullptr;
+    ieti_saddle_free(h);
     h->mem.release();
     cudaStreamSynchronize(h->st);
     if (h->h_pinned) cudaFreeHost(h->h_pinned);

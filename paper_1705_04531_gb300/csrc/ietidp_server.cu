@@ -234,7 +234,7 @@ void ietidp_server::solve_loop() {
         }
         std::vector<EngineJob*> ptr;
         for (auto& j : jobs) ptr.push_back(j.get());
-        int rc = ieti_engine_tick(E, ptr);
+        int rc = opt.method == IETIDP_METHOD_SADDLE ? ieti_saddle_tick(E, ptr) : ieti_engine_tick(E, ptr);
         std::string terr = rc == IETIDP_OK ? "" : ietidp_last_error();
         // finished (or failed) requests: copy the solution out and release
         std::vector<std::shared_ptr<Request>> keep_r;

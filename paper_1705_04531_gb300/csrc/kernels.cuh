@@ -77,7 +77,9 @@ struct SlotDesc {
     long long lv;        // offset of the slot's level vectors (3 nlvec)
 };
 
-enum SlotMode { MODE_NEUMANN = 0, MODE_BASIS = 1, MODE_SCHUR = 2, MODE_VCYCLE = 3 };
+// MODE_POWER: V-cycle contraction estimate per patch (BPCG scaling);
+// MODE_KHAT: Delta block of the BPCG preconditioner, P V^ncycles P^T / omega
+enum SlotMode { MODE_NEUMANN = 0, MODE_BASIS = 1, MODE_SCHUR = 2, MODE_VCYCLE = 3, MODE_POWER = 4, MODE_KHAT = 5 };
 
 struct SolveArgs {
     const PatchDesc* pd;
@@ -110,7 +112,9 @@ struct SolveArgs {
     int maxit;
     int nu1, nu2;
     double alpha;
-    int ncycles;               // Schur: V-cycles; V-cycle mode: cycles
+    int ncycles;               // Schur / K-hat: V-cycles; V-cycle mode: cycles
+    double theta;              // power mode: omega_k = theta (1 - rho_k^ncycles)
+    double* omega;             // per patch BPCG scaling (written by the power mode, read by K-hat)
     long long* vstats;         // [0] V-cycles, [1] V-cycle fine dofs (atomically added)
     size_t smem_bytes;         // dynamic shared memory of the launch (specialised kernels)
     int* dbg;                  // self-check record (debug builds only)

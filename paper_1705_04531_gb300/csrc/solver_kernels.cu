@@ -452,6 +452,102 @@ __global__ void __launch_bounds__(512) k_solve(SolveArgs a0) {
         return;
     }
 
+    if (a.mode == MODE_POWER || a.mode == MODE_KHAT) {
+        // fine operator of the Neumann hierarchy: K, or K + alpha M^ on
+        // floating patches (same layout as K)
+        const double* A64 = P.floating ? a.KM64 : a.K64;
+        if (a.mode == MODE_POWER) {
+            // energy-norm contraction of one V-cycle by power iteration from
+            // x_j = ((37 j) mod 101)/101 - 1/2, j the rank among the free dofs
+            const int lo0 = P.dmask & 1, lo1 = (P.dmask >> 2) & 1, lo2 = (P.dmask >> 4) & 1;
+            const int nf0 = F.m[0] - lo0 - ((P.dmask >> 1) & 1);
+            const int nf1 = F.m[1] - lo1 - ((P.dmask >> 3) & 1);
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                int i0 = i % F.m[0], i1 = (i / F.m[0]) % F.m[1], i2 = i / (F.m[0] * F.m[1]);
+                if (ieti_masked(P.dmask, F.m, i0, i1, i2)) {
+                    x[i] = 0.0;
+                } else {
+                    const long long j = (i0 - lo0) + (long long)nf0 * ((i1 - lo1) + (long long)nf1 * (i2 - (P.dim == 3 ? lo2 : 0)));
+                    x[i] = (double)((37 * j) % 101) / 101.0 - 0.5;
+                }
+            }
+            __syncthreads();
+            double rho = 0.0;
+            for (int it = 0; it < a.maxit; ++it) {
+                for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                    int i0 = i % F.m[0], i1 = (i / F.m[0]) % F.m[1], i2 = i / (F.m[0] * F.m[1]);
+                    r[i] = ieti_masked(P.dmask, F.m, i0, i1, i2) ? 0.0 : k64_row(P, A64, x, i);
+                }
+                __syncthreads();
+                vcycle_apply(vc, r, z, a.nu1, a.nu2);
+                ++vcount;
+                for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = x[i] - z[i];
+                __syncthreads();
+                double s3[3] = {0.0, 0.0, 0.0};
+                for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                    int i0 = i % F.m[0], i1 = (i / F.m[0]) % F.m[1], i2 = i / (F.m[0] * F.m[1]);
+                    const double ap = ieti_masked(P.dmask, F.m, i0, i1, i2) ? 0.0 : k64_row(P, A64, p, i);
+                    s3[0] += x[i] * r[i];
+                    s3[1] += p[i] * ap;
+                    s3[2] += p[i] * p[i];
+                }
+                cta_sum<3>(s3, red);
+                rho = s3[0] > 0.0 ? sqrt(fmax(s3[1], 0.0) / s3[0]) : 0.0;
+                const double inv = s3[2] > 0.0 ? 1.0 / sqrt(s3[2]) : 0.0;
+                for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = p[i] * inv;
+                __syncthreads();
+            }
+            if (threadIdx.x == 0) a.omega[sd.patch] = a.theta * (1.0 - pow(rho, (double)a.ncycles));
+        } else {
+            // w = P V^c P^T g / omega_k; rpi_loc holds Phi^T g per constraint row
+            const double* g = a.in + P.toff;
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                int i0 = i % F.m[0], i1 = (i / F.m[0]) % F.m[1], i2 = i / (F.m[0] * F.m[1]);
+                r[i] = ieti_masked(P.dmask, F.m, i0, i1, i2) ? 0.0 : g[i];
+            }
+            __syncthreads();
+            {
+                const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+                for (int j = w; j < P.npi; j += nw) {
+                    const int row = P.crow0 + j;
+                    const double cj = a.rpi_loc[row];
+                    for (int e = a.crow_ptr[row] + lane; e < a.crow_ptr[row + 1]; e += 32)
+                        r[a.c_idx[e]] -= a.c_w[e] * cj;
+                }
+            }
+            __syncthreads();
+            for (int c = 0; c < a.ncycles; ++c) {
+                if (c == 0) {
+                    vcycle_apply(vc, r, x, a.nu1, a.nu2);
+                } else {
+                    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                        int i0 = i % F.m[0], i1 = (i / F.m[0]) % F.m[1], i2 = i / (F.m[0] * F.m[1]);
+                        q[i] = ieti_masked(P.dmask, F.m, i0, i1, i2) ? 0.0 : r[i] - k64_row(P, A64, x, i);
+                    }
+                    __syncthreads();
+                    vcycle_apply(vc, q, z, a.nu1, a.nu2);
+                    for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] += z[i];
+                    __syncthreads();
+                }
+                ++vcount;
+            }
+            apply_C(a, P, x, coef);
+            const double sc = 1.0 / a.omega[sd.patch];
+            double* out = a.out + P.toff;
+            const double* ph = a.phi + P.phioff;
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                double u = x[i];
+                for (int j = 0; j < P.npi; ++j) u -= coef[j] * ph[(long long)j * n + i];
+                out[i] = sc * u;
+            }
+        }
+        if (threadIdx.x == 0 && a.vstats) {
+            atomicAdd((unsigned long long*)&a.vstats[0], (unsigned long long)vcount);
+            atomicAdd((unsigned long long*)&a.vstats[1], (unsigned long long)(vcount * n));
+        }
+        return;
+    }
+
     if (a.mode == MODE_VCYCLE) {
         const double* bb = a.in + P.toff;
         double* xx = a.out + P.toff;

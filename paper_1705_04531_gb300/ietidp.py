@@ -32,6 +32,7 @@ IGA_GEO_BOX, IGA_GEO_ANNULUS = 0, 1
 RHS = {"none": 0, "sin2d": 1, "sin3d": 2, "annulus": 3, "modes": 4, "quad": 5}
 PRIMAL = {"vertex": 1, "edge": 2, "face": 4}
 PREC_FP64, PREC_MIXED = 0, 1
+METHOD = {"dual": 0, "saddle": 1}
 
 
 class iga_patch_desc(C.Structure):
@@ -57,7 +58,8 @@ class ietidp_options(C.Structure):
                 ("tol_inner", C.c_double), ("tol_basis", C.c_double), ("maxit_outer", C.c_int),
                 ("maxit_inner", C.c_int), ("nu_pre", C.c_int), ("nu_post", C.c_int),
                 ("coarse_elems", C.c_int), ("dirichlet_vcycles", C.c_int), ("alpha_reg", C.c_double),
-                ("cluster", C.c_int)]
+                ("cluster", C.c_int), ("method", C.c_int), ("saddle_vcycles", C.c_int),
+                ("saddle_theta", C.c_double)]
 
 
 class ietidp_stats(C.Structure):
@@ -209,6 +211,8 @@ def default_options(**kw) -> ietidp_options:
             v = primal_mask(v)
         if k == "precision" and isinstance(v, str):
             v = PREC_MIXED if v == "mixed" else PREC_FP64
+        if k == "method" and isinstance(v, str):
+            v = METHOD[v]
         setattr(o, k, v)
     return o
 

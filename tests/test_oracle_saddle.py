@@ -30,6 +30,7 @@ DOMS = {
     "grid3_floating": lambda: W.random_quad_rhs(W.uniform_grid(2, (3, 3), 2, 8, W.UNIT, None,
                                                                ("vertex", "edge")), seed=22),
     "cube": lambda: W.random_quad_rhs(W.cube_2x2x2(4, 2), seed=23),
+    "uneven3x3": lambda: W.random_quad_rhs(W.uneven_8x8(0, grid=(3, 3), nelems=(8, 16, 32)), seed=32),
 }
 
 
@@ -124,7 +125,7 @@ def test_contraction_estimate_bounds_block_condition():
         rho_exact = np.abs(np.linalg.eigvals(Lc.T @ E @ np.linalg.inv(Lc.T))).max()
         rho_est = saddle.vcycle_contraction(mg)
         assert rho_est <= rho_exact * (1 + 1e-6)
-        assert rho_est >= 0.9 * rho_exact, (rho_est, rho_exact)
+        assert rho_est >= 0.98 * rho_exact, (rho_est, rho_exact)
 
 
 def test_bpcg_iterations_exceed_dual_cg_moderately():
