@@ -52,9 +52,11 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--vcycle-reps", type=int, default=50)
-    ap.add_argument("--mode", default="bench", choices=["bench", "vcycle", "serve"],
+    ap.add_argument("--mode", default="bench", choices=["bench", "vcycle", "serve", "profile"],
                     help="vcycle: setup plus three batched V-cycle launches (profiling target); "
-                         "serve: Poisson-arrival request stream through the continuous-batching server")
+                         "serve: Poisson-arrival request stream through the continuous-batching server; "
+                         "profile: one batched solve of --batch copies inside a profiler range "
+                         "(cudaProfilerStart/Stop), after a warm-up solve")
     ap.add_argument("--rate", type=float, default=100.0, help="serve: arrivals per second")
     ap.add_argument("--nreq", type=int, default=64, help="serve: requests in the stream")
     ap.add_argument("--concurrency", type=int, default=8, help="serve: worker streams")
@@ -251,7 +253,7 @@ def time_path(api, torch, prob, prec, args, flush, stream):
     return sol, u, ms, stats, setup_ms
 
 
-def time_batch(api, torch, dom, prec, args, flush, stream):
+def time_batch(api, torch, dom, prec, args, flush, stream, method="dual"):
     """B independent copies of the workload (own assembled problem and handle
     each) solved in lockstep by ietidp_solve_batch: one step = B complete
     solves, their local solves merged into shared launches.  Timed with CUDA
@@ -259,7 +261,7 @@ def time_batch(api, torch, dom, prec, args, flush, stream):
     B = args.batch
     t0 = time.perf_counter()
     probs = [api.Problem(dom) for _ in range(B)]
-    sols = [api.Solver(p, precision=prec) for p in probs]
+    sols = [api.Solver(p, precision=prec, method=method) for p in probs]
     torch.cuda.synchronize()
     setup_ms = 1e3 * (time.perf_counter() - t0) / B
     fs = [p.load() for p in probs]
@@ -369,6 +371,34 @@ def run_serve(args):
 
 
 
+def run_profile(args):
+    """A warm-up batched solve (autotuning included), then one batched solve
+    of --batch copies of the workload inside a profiler range, so that
+    ``ncu --profile-from-start off -k regex:k_solve_t -c 1`` captures the
+    first merged local-solve launch of a tuned, steady-state solve."""
+    import torch
+    from paper_1705_04531_gb300 import build
+    build.build()
+    from paper_1705_04531_gb300 import ietidp as api
+    dom = workload(args.workload)
+    probs = [api.Problem(dom) for _ in range(args.batch)]
+    sols = [api.Solver(p, precision=args.precision) for p in probs]
+    api.Solver.solve_batch(sols)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    _, sts = api.Solver.solve_batch(sols)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    p, ne = dom.patch_degree(0), dom.patch_nelem(0)
+    its = sum(st["inner_its"] for st in sts)
+    nl = sts[0]["neumann_launches"]
+    print(json.dumps({"mode": "profile", "workload": args.workload, "batch": args.batch,
+                      "precision": args.precision, "neumann_launches": nl,
+                      "cg_iterations_per_launch": its / max(1, nl),
+                      "alg_bytes_per_cg_iteration": bytes_per_iteration(ne, p, 4 if args.precision == "mixed" else 8),
+                      "autotune": api.autotune_table()}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -377,6 +407,8 @@ def main():
         return run_vcycle_probe(args)
     if args.mode == "serve":
         return run_serve(args)
+    if args.mode == "profile":
+        return run_profile(args)
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -462,9 +494,20 @@ def main():
         e2e_t.append(time.perf_counter() - t)
     e2e_val = world * args.batch * len(e2e_t) / sum(e2e_t)
     achieved, alg_bytes_per_launch, launch_ms, nlaunch = roofline(bt, dom, 4)
-    tune = api.autotune_table()
     sts = bt["stats"]
     close_batch(bt)
+
+    # MG-MG-S (BPCG on the saddle-point system, 3 V-cycles in the K~
+    # preconditioner), batched mixed path on the same workload
+    bs = time_batch(api, torch, dom, "mixed", args, flush, stream, method="saddle")
+    saddle_err = max(relerr(bs["sols"][i].split(bs["us"][i]), u64h) for i in range(args.batch))
+    saddle = {"value": world * args.batch * args.steps / (sum(bs["ms"]) / 1e3),
+              "ms_per_step": sum(bs["ms"]) / args.steps,
+              "outer_it": bs["stats"][-1][0]["outer_it"], "vcycles_per_solve": bs["stats"][-1][0]["vcycles"],
+              "rel_err_vs_fp64_dual": saddle_err,
+              "note": "MG-MG-S: Bramble-Pasciak CG on Eq. 2, mixed V-cycles, same batch and tolerance"}
+    close_batch(bs)
+    tune = api.autotune_table()
 
     if rank != 0:
         if dist:
@@ -509,6 +552,7 @@ def main():
                  "setup_ms": setup64, "batch_vs_single_rel_err": b64_err,
                  "roofline_achieved_gbs": ach64, "launch_ms": lms64},
         "mixed_over_fp64": sum(bt64["ms"]) / tot,
+        "mg_mg_s": saddle,
         "vcycle_dofs_per_s": vcycle_dofs_s, "vcycle_ms": vc_ms,
         "roofline": {"bound": "hbm", "kernel": "k_solve_t<float,2,3,3,0> (merged Neumann PCG + V-cycles)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
