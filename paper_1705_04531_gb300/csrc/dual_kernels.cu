@@ -178,6 +178,7 @@ __global__ void k_outer_init(int n, const double* d, double* lam, double* r, dou
     if (threadIdx.x == 0) {
         st[5] = s[0];
         st[4] = s[0];
+        st[6] = 0.0;   // completed steps (history index of the next one)
     }
 }
 
@@ -208,10 +209,13 @@ __global__ void k_outer_step1(int n, const double* p, const double* q, double* l
     }
     cta_sum<1>(s2, sh);
     if (threadIdx.x == 0) {
+        // it < 0: the step counter kept in st[6] (replayable launches)
+        const int k = it >= 0 ? it : (int)st[6];
         st[1] = s[0];
         st[2] = alpha;
         st[4] = s2[0];
-        hist[2 * it] = alpha;
+        st[6] = (double)(k + 1);
+        hist[2 * k] = alpha;
     }
 }
 
@@ -225,9 +229,10 @@ __global__ void k_outer_step2(int n, const double* r, const double* z, double* p
     for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = z[i] + beta * p[i];
     __syncthreads();
     if (threadIdx.x == 0) {
+        const int k = it >= 0 ? it : (int)st[6] - 1;
         st[0] = s[0];
         st[3] = beta;
-        hist[2 * it + 1] = beta;
+        hist[2 * k + 1] = beta;
     }
 }
 
@@ -237,10 +242,63 @@ __global__ void k_axpy(long long n, const double* a, double s, const double* b, 
         out[i] = a[i] + s * b[i];
 }
 
+// y = K x per patch (fine level, Dirichlet rows zero).  Rows are visited in
+// storage order (color by color), so that each stencil diagonal is read with
+// unit stride from the color-blocked value array.
 __global__ void k_apply_K(const PatchDesc* pd, const double* K64, const double* x, double* y) {
+    __shared__ int coff[(IETI_MAXP + 1) * (IETI_MAXP + 1) * (IETI_MAXP + 1) + 1];
     const PatchDesc& P = pd[blockIdx.y];
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x)
-        y[P.toff + i] = k64_apply_row(P, K64, x + P.toff, i);
+    const LevelDesc& L = P.lev[P.L - 1];
+    const int C0 = P.p[0] + 1, C1 = P.p[1] + 1, C2 = P.p[2] + 1, NC = C0 * C1 * C2;
+    const int W0 = 2 * P.p[0] + 1, W1 = 2 * P.p[1] + 1;
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int c = 0; c < NC; ++c) {
+            coff[c] = acc;
+            acc += ieti_cnt(L.m[0], P.p[0], c % C0) * ieti_cnt(L.m[1], P.p[1], (c / C0) % C1) *
+                   ieti_cnt(L.m[2], P.p[2], c / (C0 * C1));
+        }
+        coff[NC] = acc;
+    }
+    __syncthreads();
+    const double* vals = K64 + L.koff;
+    const double* xp = x + P.toff;
+    double* yp = y + P.toff;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < L.n; s += gridDim.x * blockDim.x) {
+        int lo = 0, hi = NC - 1;   // color: last c with coff[c] <= s
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (coff[mid] <= s) lo = mid;
+            else hi = mid - 1;
+        }
+        const int c = lo, c0 = c % C0, c1 = (c / C0) % C1, c2 = c / (C0 * C1);
+        const int k0 = ieti_cnt(L.m[0], P.p[0], c0), k1 = ieti_cnt(L.m[1], P.p[1], c1);
+        const int cnt = coff[c + 1] - coff[c];
+        const int q = s - coff[c];
+        const int t0 = q % k0, tr = q / k0, t1 = tr % k1, t2 = tr / k1;
+        const int i0 = c0 + C0 * t0, i1 = c1 + C1 * t1, i2 = c2 + C2 * t2;
+        const int i = i0 + L.m[0] * (i1 + L.m[1] * i2);
+        if (ieti_masked(P.dmask, L.m, i0, i1, i2)) {
+            yp[i] = 0.0;
+            continue;
+        }
+        const double* v = vals + (long long)coff[c] * L.S + q;
+        double acc = 0.0;
+        int o = 0;
+        for (int o2 = -P.p[2]; o2 <= P.p[2]; ++o2) {
+            const bool ok2 = (unsigned)(i2 + o2) < (unsigned)L.m[2];
+            for (int o1 = -P.p[1]; o1 <= P.p[1]; ++o1) {
+                const bool ok1 = ok2 && (unsigned)(i1 + o1) < (unsigned)L.m[1];
+                const int xb = i0 + L.m[0] * ((i1 + o1) + L.m[1] * (i2 + o2));
+                for (int o0 = -P.p[0]; o0 <= P.p[0]; ++o0, ++o) {
+                    if (ok1 && (unsigned)(i0 + o0) < (unsigned)L.m[0]) acc += v[(long long)o * cnt] * xp[xb + o0];
+                }
+            }
+        }
+        (void)W0;
+        (void)W1;
+        yp[i] = acc;
+    }
 }
 
 int grid_for(long long n, int threads, int cap = 152 * 16) {
@@ -327,6 +385,6 @@ cudaError_t launch_axpy_torn(long long n, const double* a, double s, const doubl
 }
 cudaError_t launch_apply_K(const PatchDesc* pd, int npatch, const double* K64, const double* x, double* y,
                            cudaStream_t st) {
-    k_apply_K<<<dim3(16, npatch), 256, 0, st>>>(pd, K64, x, y);
+    k_apply_K<<<dim3(32, npatch), 256, 0, st>>>(pd, K64, x, y);
     return cudaGetLastError();
 }

@@ -23,7 +23,9 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <cstdint>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <numeric>
 #include <tuple>
@@ -54,6 +56,7 @@ struct TuneCfg {
     size_t smem;
     int ctas_per_sm;
     float ms;
+    int xg;   // V-cycle vectors in global memory (fewer bytes of shared memory per CTA)
 };
 
 std::mutex g_tune_mu;
@@ -82,7 +85,8 @@ struct MGroup {
     std::vector<long long> cost;
     size_t smem = 0;       // shared memory of the handles' own plan (max)
     size_t smem_min = 0;   // shared memory the kernel cannot do without (max)
-    TuneCfg cfg{512, 0, 1, 0.f};
+    size_t tab_min = 0;    // color tables alone (minimum of the global-vector variant)
+    TuneCfg cfg{512, 0, 1, 0.f, 0};
 };
 
 }  // namespace
@@ -99,7 +103,16 @@ struct Staging {   // pinned and device copies of one launch stage's arguments a
     size_t cap_slots = 0;
 };
 
+struct GraphEntry {   // one captured launch segment
+    cudaGraphExec_t exec = nullptr;   // null: the segment could not be captured
+    std::vector<long long> dl;        // per job: kernel launches of one replay
+    long long total = 0;              // kernels of one replay
+};
+
 struct ieti_engine {
+    bool own_stream = false;   // the stream was created for the engine (destroyed with it)
+    std::map<std::vector<uintptr_t>, std::unique_ptr<GraphEntry>> graphs;
+    std::map<std::vector<uintptr_t>, int> seen;
     cudaStream_t st = nullptr;
     std::vector<cudaStream_t> side;
     std::vector<cudaEvent_t> join;
@@ -139,6 +152,13 @@ void free_staging(ieti_engine* E, Staging& S) {
     S = Staging{};
 }
 
+void clear_graphs(ieti_engine* E) {
+    for (auto& kv : E->graphs)
+        if (kv.second->exec) cudaGraphExecDestroy(kv.second->exec);
+    E->graphs.clear();
+    E->seen.clear();
+}
+
 int ensure_side(ieti_engine* E, size_t n) {
     while (E->side.size() < std::min<size_t>(n, 8)) {
         cudaStream_t s;
@@ -155,24 +175,31 @@ cudaError_t launch_cfg(const SolveArgs& a, const MGroup& g, const TuneCfg& c, cu
     SolveArgs b = a;
     b.smem_bytes = c.smem;
     if (g.kind == 2) return launch_solve(b, c.threads, st);
-    return launch_solve_variant(b, g.dim, g.p0, g.p1, g.p2, c.threads, st, g.kind == 1);
+    return launch_solve_variant(b, g.dim, g.p0, g.p1, g.p2, c.threads, st, g.kind == 1 || c.xg);
 }
 
 // candidate configurations of a merged launch: 512 threads with the full
 // budget, or fewer threads with a budget that lets 2 or 3 CTAs share an SM
 std::vector<TuneCfg> candidates(const MGroup& g) {
     std::vector<TuneCfg> c;
-    c.push_back(TuneCfg{512, g.smem, 1, 0.f});
+    c.push_back(TuneCfg{512, g.smem, 1, 0.f, 0});
     if (g.kind == 2) return c;
-    const int want[2] = {2, 3};
-    const int thr[2] = {256, 128};
-    for (int k = 0; k < 2; ++k) {
+    // (threads, CTAs per SM, vectors in global memory): the vectors of a
+    // patch need shared memory only in the shared-vector variant, so the
+    // global-vector variant reaches more CTAs per SM
+    const int thr[5] = {256, 128, 256, 128, 128};
+    const int want[5] = {2, 3, 2, 3, 4};
+    const int xg[5] = {0, 0, 1, 1, 1};
+    for (int k = 0; k < 5; ++k) {
+        const bool gx = g.kind == 1 || xg[k];
+        if (g.kind == 1 && !xg[k]) continue;   // global-vector groups: listed once
+        const size_t lo = gx ? g.tab_min : g.smem_min;
         // largest budget (in 4 KB steps) at which `want` CTAs fit on an SM
         for (size_t b = std::min(g.smem, (size_t)kSmemCap / want[k]); b >= 16 * 1024; b -= 4 * 1024) {
-            if (b < g.smem_min) break;
-            int occ = solve_variant_ctas_per_sm(g.dim, g.p0, g.p1, g.p2, g.mixed, g.kind == 1, thr[k], b);
+            if (b < lo) break;
+            int occ = solve_variant_ctas_per_sm(g.dim, g.p0, g.p1, g.p2, g.mixed, gx, thr[k], b);
             if (occ >= want[k]) {
-                c.push_back(TuneCfg{thr[k], b, occ, 0.f});
+                c.push_back(TuneCfg{thr[k], b, occ, 0.f, xg[k]});
                 break;
             }
         }
@@ -183,7 +210,7 @@ std::vector<TuneCfg> candidates(const MGroup& g) {
 // time each candidate on one V-cycle per slot (zero data, same work as a
 // real launch) and keep the fastest; cached per launch shape
 int tune(ieti_engine* E, MGroup& g, const std::vector<ietidp_handle*>& hs, long long* nlaunch) {
-    g.cfg = TuneCfg{512, g.smem, 1, 0.f};
+    g.cfg = TuneCfg{512, g.smem, 1, 0.f, 0};
     if (g.kind == 2 || !autotune_enabled()) return IETIDP_OK;
     TuneKey key{g.dim, g.p0, g.p1, g.p2, g.kind, g.mixed,
                 (int)((g.s.size() + sm_count() - 1) / sm_count()),
@@ -192,7 +219,7 @@ int tune(ieti_engine* E, MGroup& g, const std::vector<ietidp_handle*>& hs, long 
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune.find(key);
         if (it != g_tune.end()) {
-            if (it->second.smem >= g.smem_min) {
+            if (it->second.smem >= (it->second.xg ? g.tab_min : g.smem_min)) {
                 g.cfg = it->second;
                 g.cfg.smem = std::min(g.cfg.smem, g.smem);
             }
@@ -282,6 +309,7 @@ int merged_launch(ieti_engine* E, Staging& S, std::vector<std::pair<ietidp_handl
                 m.s.push_back(sd);
                 m.cost.push_back((long long)P.n * P.lev[P.L - 1].S);
                 m.smem_min = std::max(m.smem_min, kind == 1 ? solve_smem_tables(P) : solve_smem_min(P, mixed));
+                m.tab_min = std::max(m.tab_min, solve_smem_tables(P));
             }
         }
     }
@@ -466,6 +494,7 @@ int ieti_engine_create(cudaStream_t st, ieti_engine** out) {
 void ieti_engine_destroy(ieti_engine* E) {
     if (!E) return;
     cudaStreamSynchronize(E->st);
+    clear_graphs(E);
     free_staging(E, E->stA);
     free_staging(E, E->stB);
     free_staging(E, E->stT);
@@ -478,6 +507,7 @@ void ieti_engine_destroy(ieti_engine* E) {
     if (E->e1) cudaEventDestroy(E->e1);
     if (E->t0) cudaEventDestroy(E->t0);
     if (E->t1) cudaEventDestroy(E->t1);
+    if (E->own_stream) cudaStreamDestroy(E->st);
     delete E;
 }
 
@@ -490,6 +520,192 @@ void ieti_engine_job_init(EngineJob& j, ietidp_handle* h, const double* f, doubl
     j.u = u;
     j.t0 = std::chrono::steady_clock::now();
 }
+
+namespace {
+
+// The small per-job launches of a tick stage (before and after its merged
+// launch) are enqueued by these segment functions; the merged launches
+// themselves run eagerly between them (timed with the engine's events).
+//   segment 0: stage A inputs (B^T p, primal restriction / coarse solve, ...)
+//   segment 1: stage A outputs (B u, outer CG step, read-back)
+//   segment 2: stage B input (B_D^T r)
+//   segment 3: stage B outputs (B_D w, next search direction)
+bool in_A(const EngineJob* j) {
+    return j->phase == EngineJob::INIT || j->phase == EngineJob::ITER || j->phase == EngineJob::RECOVER;
+}
+bool in_B(const EngineJob* j) { return j->phase == EngineJob::PRECF || j->phase == EngineJob::PREC; }
+
+int segment(ieti_engine* E, int seg, std::vector<EngineJob*>& jobs, const std::vector<size_t>& rbo) {
+    cudaStream_t st = E->st;
+    for (size_t i = 0; i < jobs.size(); ++i) {
+        EngineJob* j = jobs[i];
+        ietidp_handle* h = j->h;
+        if (seg == 0) {
+            if (j->phase == EngineJob::INIT) {
+                CU(cudaMemsetAsync(h->flags, 0, sizeof(int), st));
+                CU(cudaMemsetAsync(h->vst, 0, sizeof(long long) * 8, st));
+                CHK(primal(h, j->f, st, *j));
+            } else if (j->phase == EngineJob::ITER) {
+                LCHK(launch_bt(h->dual, h->p, h->gF, 0, st));
+                count(*j, 1);
+                CHK(primal(h, h->gF, st, *j));
+            } else if (j->phase == EngineJob::RECOVER) {
+                LCHK(launch_bt(h->dual, h->lam, h->tmp, 0, st));
+                LCHK(launch_axpy_torn(h->prob->ntorn, j->f, -1.0, h->tmp, h->gR, st));
+                count(*j, 2);
+                CHK(primal(h, h->gR, st, *j));
+            }
+        } else if (seg == 1) {
+            double* rb = E->h_rb + rbo[i];
+            if (j->phase == EngineJob::INIT) {
+                if (h->nlam > 0) {
+                    LCHK(launch_b(h->dual, j->u, h->d, 0, st));
+                    LCHK(launch_jump_scale(h->dual, j->u, h->scal, st));
+                    LCHK(launch_outer_init(h->nlam, h->d, h->lam, h->r, h->state, st));
+                    count(*j, 3);
+                    CU(cudaMemcpyAsync(rb, h->state + 5, sizeof(double), cudaMemcpyDeviceToHost, st));
+                    CU(cudaMemcpyAsync(rb + 1, h->scal, sizeof(double), cudaMemcpyDeviceToHost, st));
+                }
+                CU(cudaMemcpyAsync(rb + 2, h->flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+                CU(cudaMemcpyAsync(rb + 8, h->vst, sizeof(long long) * 8, cudaMemcpyDeviceToHost, st));
+            } else if (j->phase == EngineJob::ITER) {
+                LCHK(launch_b(h->dual, h->uF, h->q, 0, st));
+                LCHK(launch_outer_step1(h->nlam, h->p, h->q, h->lam, h->r, h->state, h->hist, -1, st));
+                count(*j, 2);
+                CU(cudaMemcpyAsync(rb, h->state + 4, sizeof(double), cudaMemcpyDeviceToHost, st));
+            } else if (j->phase == EngineJob::RECOVER) {
+                CU(cudaMemcpyAsync(rb + 2, h->flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+                CU(cudaMemcpyAsync(rb + 8, h->vst, sizeof(long long) * 8, cudaMemcpyDeviceToHost, st));
+                if (j->it > 0)
+                    CU(cudaMemcpyAsync(rb + kRb, h->hist, sizeof(double) * 2 * j->it, cudaMemcpyDeviceToHost, st));
+            }
+        } else if (seg == 2) {
+            if (!in_B(j)) continue;
+            LCHK(launch_bt(h->dual, h->r, h->vS, 1, st));
+            count(*j, 1);
+        } else {
+            if (!in_B(j)) continue;
+            LCHK(launch_b(h->dual, h->wS, h->z, 1, st));
+            if (j->phase == EngineJob::PRECF) {
+                LCHK(launch_outer_first(h->nlam, h->r, h->z, h->p, h->state, st));
+            } else {
+                LCHK(launch_outer_step2(h->nlam, h->r, h->z, h->p, h->state, h->hist, -1, st));
+            }
+            count(*j, 2);
+        }
+    }
+    return IETIDP_OK;
+}
+
+// merged local-solve launch of stage A (Neumann) or B (Dirichlet), eager;
+// stage A is bracketed by the engine's events
+int merged_stage(ieti_engine* E, int stage, std::vector<EngineJob*>& jobs) {
+    std::vector<std::pair<ietidp_handle*, SolveArgs>> items;
+    std::vector<EngineJob*> in;
+    for (EngineJob* j : jobs) {
+        ietidp_handle* h = j->h;
+        if (stage == 0) {
+            if (j->phase == EngineJob::INIT)
+                items.emplace_back(h, ieti_solve_args(h, MODE_NEUMANN, j->f, j->u, h->opt.tol_inner,
+                                                      h->opt.maxit_inner, h->vst));
+            else if (j->phase == EngineJob::ITER)
+                items.emplace_back(h, ieti_solve_args(h, MODE_NEUMANN, h->gF, h->uF, h->opt.tol_inner,
+                                                      h->opt.maxit_inner, h->vst));
+            else if (j->phase == EngineJob::RECOVER)
+                items.emplace_back(h, ieti_solve_args(h, MODE_NEUMANN, h->gR, j->u, h->opt.tol_inner,
+                                                      h->opt.maxit_inner, h->vst));
+            else
+                continue;
+        } else {
+            if (!in_B(j)) continue;
+            items.emplace_back(h, ieti_solve_args(h, MODE_SCHUR, h->vS, h->wS, 0.0, 0, h->vst));
+        }
+        in.push_back(j);
+    }
+    if (items.empty()) return IETIDP_OK;
+    long long nl = 0;
+    if (stage == 0) CU(cudaEventRecord(E->e0, E->st));
+    CHK(merged_launch(E, stage == 0 ? E->stA : E->stB, items, &nl));
+    if (stage == 0) CU(cudaEventRecord(E->e1, E->st));
+    ieti_host::g_kernel_launches += nl;
+    for (EngineJob* j : in) {
+        j->S.launches += nl;
+        if (stage == 0) j->S.neumann_launches += 1;
+    }
+    return IETIDP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// CUDA graphs of the per-job launch segments: a segment whose launch sequence
+// repeats (same jobs, same phases: every steady-state outer iteration) is
+// captured on its second occurrence and replayed from then on as one graph
+// launch.  IETIDP_GRAPHS=0 disables capture.
+// ---------------------------------------------------------------------------
+bool graphs_enabled() {
+    const char* e = std::getenv("IETIDP_GRAPHS");
+    return !(e && e[0] == '0');
+}
+
+std::vector<uintptr_t> segment_key(ieti_engine* E, int seg, const std::vector<EngineJob*>& jobs) {
+    std::vector<uintptr_t> k;
+    k.push_back((uintptr_t)seg);
+    k.push_back((uintptr_t)E->h_rb);
+    for (EngineJob* j : jobs) {
+        k.push_back((uintptr_t)j->h);
+        k.push_back((uintptr_t)j->phase);
+        k.push_back((uintptr_t)j->f);
+        k.push_back((uintptr_t)j->u);
+        k.push_back((uintptr_t)(j->phase == EngineJob::RECOVER ? j->it : 0));
+    }
+    return k;
+}
+
+int staged(ieti_engine* E, int seg, std::vector<EngineJob*>& jobs, const std::vector<size_t>& rbo) {
+    auto eager = [&]() { return segment(E, seg, jobs, rbo); };
+    if (!graphs_enabled()) return eager();
+    const auto key = segment_key(E, seg, jobs);
+    auto it = E->graphs.find(key);
+    if (it != E->graphs.end() && it->second->exec) {
+        GraphEntry& G = *it->second;
+        CU(cudaGraphLaunch(G.exec, E->st));
+        for (size_t i = 0; i < jobs.size(); ++i) jobs[i]->S.launches += G.dl[i];
+        ieti_host::g_kernel_launches += G.total;
+        return IETIDP_OK;
+    }
+    if (it != E->graphs.end() || ++E->seen[key] < 2) return eager();
+    if (E->graphs.size() >= 256) clear_graphs(E);
+    auto G = std::make_unique<GraphEntry>();
+    std::vector<long long> l0(jobs.size());
+    for (size_t i = 0; i < jobs.size(); ++i) l0[i] = jobs[i]->S.launches;
+    const long long g0 = ieti_host::g_kernel_launches.load();
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(E->st, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+        cudaGetLastError();
+        E->graphs[key] = std::move(G);   // not capturable: eager from now on
+        return eager();
+    }
+    int rc = eager();
+    cudaError_t e = cudaStreamEndCapture(E->st, &graph);
+    if (rc == IETIDP_OK && e == cudaSuccess && graph) e = cudaGraphInstantiate(&G->exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (rc != IETIDP_OK || e != cudaSuccess || !G->exec) {
+        cudaGetLastError();
+        if (G->exec) cudaGraphExecDestroy(G->exec);
+        G->exec = nullptr;
+        for (size_t i = 0; i < jobs.size(); ++i) jobs[i]->S.launches = l0[i];
+        ieti_host::g_kernel_launches = g0;
+        E->graphs[key] = std::move(G);
+        return eager();
+    }
+    G->dl.resize(jobs.size());
+    for (size_t i = 0; i < jobs.size(); ++i) G->dl[i] = jobs[i]->S.launches - l0[i];
+    G->total = ieti_host::g_kernel_launches.load() - g0;
+    CU(cudaGraphLaunch(G->exec, E->st));
+    E->graphs[key] = std::move(G);
+    return IETIDP_OK;
+}
+
+}  // namespace
 
 int ieti_engine_tick(ieti_engine* E, std::vector<EngineJob*>& jobs) {
     cudaStream_t st = E->st;
@@ -507,79 +723,22 @@ int ieti_engine_tick(ieti_engine* E, std::vector<EngineJob*>& jobs) {
         E->cap_rb = 0;
         CU(cudaMallocHost((void**)&E->h_rb, sizeof(double) * std::max(need, (size_t)256)));
         E->cap_rb = std::max(need, (size_t)256);
+        clear_graphs(E);   // captured read-backs point at the old buffer
     }
-    long long nl = 0;
-    // ---- stage A: local Neumann solves --------------------------------------
-    std::vector<std::pair<ietidp_handle*, SolveArgs>> A;
-    std::vector<EngineJob*> inA;
-    for (EngineJob* j : jobs) {
-        ietidp_handle* h = j->h;
-        if (j->phase == EngineJob::INIT) {
-            CU(cudaMemsetAsync(h->flags, 0, sizeof(int), st));
-            CU(cudaMemsetAsync(h->vst, 0, sizeof(long long) * 8, st));
-            CHK(primal(h, j->f, st, *j));
-            A.emplace_back(h, ieti_solve_args(h, MODE_NEUMANN, j->f, j->u, h->opt.tol_inner, h->opt.maxit_inner,
-                                              h->vst));
-        } else if (j->phase == EngineJob::ITER) {
-            LCHK(launch_bt(h->dual, h->p, h->gF, 0, st));
-            count(*j, 1);
-            CHK(primal(h, h->gF, st, *j));
-            A.emplace_back(h, ieti_solve_args(h, MODE_NEUMANN, h->gF, h->uF, h->opt.tol_inner, h->opt.maxit_inner,
-                                              h->vst));
-        } else if (j->phase == EngineJob::RECOVER) {
-            LCHK(launch_bt(h->dual, h->lam, h->tmp, 0, st));
-            LCHK(launch_axpy_torn(h->prob->ntorn, j->f, -1.0, h->tmp, h->gR, st));
-            count(*j, 2);
-            CHK(primal(h, h->gR, st, *j));
-            A.emplace_back(h, ieti_solve_args(h, MODE_NEUMANN, h->gR, j->u, h->opt.tol_inner, h->opt.maxit_inner,
-                                              h->vst));
-        } else {
-            continue;
-        }
-        inA.push_back(j);
-    }
-    if (!A.empty()) {
-        long long n0 = nl;
-        CU(cudaEventRecord(E->e0, st));
-        CHK(merged_launch(E, E->stA, A, &nl));
-        CU(cudaEventRecord(E->e1, st));
-        ieti_host::g_kernel_launches += nl - n0;
-        for (EngineJob* j : inA) {
-            j->S.launches += nl - n0;
-            j->S.neumann_launches += 1;
-        }
-    }
-    for (size_t i = 0; i < jobs.size(); ++i) {
-        EngineJob* j = jobs[i];
-        ietidp_handle* h = j->h;
-        double* rb = E->h_rb + rbo[i];
-        if (j->phase == EngineJob::INIT) {
-            if (h->nlam > 0) {
-                LCHK(launch_b(h->dual, j->u, h->d, 0, st));
-                LCHK(launch_jump_scale(h->dual, j->u, h->scal, st));
-                LCHK(launch_outer_init(h->nlam, h->d, h->lam, h->r, h->state, st));
-                count(*j, 3);
-                CU(cudaMemcpyAsync(rb, h->state + 5, sizeof(double), cudaMemcpyDeviceToHost, st));
-                CU(cudaMemcpyAsync(rb + 1, h->scal, sizeof(double), cudaMemcpyDeviceToHost, st));
-            }
-            CU(cudaMemcpyAsync(rb + 2, h->flags, sizeof(int), cudaMemcpyDeviceToHost, st));
-            CU(cudaMemcpyAsync(rb + 8, h->vst, sizeof(long long) * 8, cudaMemcpyDeviceToHost, st));
-        } else if (j->phase == EngineJob::ITER) {
-            LCHK(launch_b(h->dual, h->uF, h->q, 0, st));
-            LCHK(launch_outer_step1(h->nlam, h->p, h->q, h->lam, h->r, h->state, h->hist, j->it - 1, st));
-            count(*j, 2);
-            CU(cudaMemcpyAsync(rb, h->state + 4, sizeof(double), cudaMemcpyDeviceToHost, st));
-        } else if (j->phase == EngineJob::RECOVER) {
-            CU(cudaMemcpyAsync(rb + 2, h->flags, sizeof(int), cudaMemcpyDeviceToHost, st));
-            CU(cudaMemcpyAsync(rb + 8, h->vst, sizeof(long long) * 8, cudaMemcpyDeviceToHost, st));
-            if (j->it > 0)
-                CU(cudaMemcpyAsync(rb + kRb, h->hist, sizeof(double) * 2 * j->it, cudaMemcpyDeviceToHost, st));
-        }
-    }
+    bool anyA = false;
+    for (EngineJob* j : jobs) anyA = anyA || in_A(j);
+    CHK(staged(E, 0, jobs, rbo));
+    CHK(merged_stage(E, 0, jobs));
+    CHK(staged(E, 1, jobs, rbo));
     CU(cudaStreamSynchronize(st));
     float msA = 0.f;
-    if (!A.empty()) cudaEventElapsedTime(&msA, E->e0, E->e1);
-    for (EngineJob* j : inA) j->S.neumann_ms += msA;
+    if (anyA && cudaEventElapsedTime(&msA, E->e0, E->e1) != cudaSuccess) {
+        cudaGetLastError();
+        msA = 0.f;
+    }
+    for (EngineJob* j : jobs)
+        if (j->phase == EngineJob::INIT || j->phase == EngineJob::ITER || j->phase == EngineJob::RECOVER)
+            j->S.neumann_ms += msA;
     // ---- host decisions --------------------------------------------------------
     for (size_t i = 0; i < jobs.size(); ++i) {
         EngineJob* j = jobs[i];
@@ -639,35 +798,17 @@ int ieti_engine_tick(ieti_engine* E, std::vector<EngineJob*>& jobs) {
             finish(*j);
         }
     }
-    // ---- stage B: scaled Dirichlet preconditioner ---------------------------------
-    std::vector<std::pair<ietidp_handle*, SolveArgs>> B;
-    std::vector<EngineJob*> inB;
+    CHK(staged(E, 2, jobs, rbo));
+    CHK(merged_stage(E, 1, jobs));
+    CHK(staged(E, 3, jobs, rbo));
     for (EngineJob* j : jobs) {
-        if (j->phase != EngineJob::PRECF && j->phase != EngineJob::PREC) continue;
-        ietidp_handle* h = j->h;
-        LCHK(launch_bt(h->dual, h->r, h->vS, 1, st));
-        count(*j, 1);
-        B.emplace_back(h, ieti_solve_args(h, MODE_SCHUR, h->vS, h->wS, 0.0, 0, h->vst));
-        inB.push_back(j);
-    }
-    if (!B.empty()) {
-        long long n0 = nl;
-        CHK(merged_launch(E, E->stB, B, &nl));
-        ieti_host::g_kernel_launches += nl - n0;
-        for (EngineJob* j : inB) j->S.launches += nl - n0;
-    }
-    for (EngineJob* j : inB) {
-        ietidp_handle* h = j->h;
-        LCHK(launch_b(h->dual, h->wS, h->z, 1, st));
         if (j->phase == EngineJob::PRECF) {
-            LCHK(launch_outer_first(h->nlam, h->r, h->z, h->p, h->state, st));
             j->it = 1;
-        } else {
-            LCHK(launch_outer_step2(h->nlam, h->r, h->z, h->p, h->state, h->hist, j->it - 1, st));
+            j->phase = EngineJob::ITER;
+        } else if (j->phase == EngineJob::PREC) {
             j->it += 1;
+            j->phase = EngineJob::ITER;
         }
-        count(*j, 2);
-        j->phase = EngineJob::ITER;
     }
     return IETIDP_OK;
 }
@@ -720,7 +861,7 @@ extern "C" int ietidp_autotune_table(int* out, int max_entries) {
     int n = 0;
     for (const auto& kv : g_tune) {
         if (out && n < max_entries) {
-            int* o = out + 10 * n;
+            int* o = out + 11 * n;
             o[0] = kv.first.dim;
             o[1] = kv.first.p0;
             o[2] = kv.first.p1;
@@ -731,6 +872,7 @@ extern "C" int ietidp_autotune_table(int* out, int max_entries) {
             o[7] = kv.second.threads;
             o[8] = (int)kv.second.smem;
             o[9] = kv.second.ctas_per_sm;
+            o[10] = kv.first.kind == 1 || kv.second.xg;
         }
         ++n;
     }
@@ -742,8 +884,20 @@ extern "C" int ietidp_autotune_table(int* out, int max_entries) {
 // ---------------------------------------------------------------------------
 namespace {
 
+// the handle's engine works on a non-blocking stream of its own (the
+// caller's stream may be the legacy default stream, which cannot be
+// captured into a graph); run_jobs joins it with the handles' streams
 int engine_of(ietidp_handle* h, ieti_engine** E) {
-    if (!h->engine) CHK(ieti_engine_create(h->st, &h->engine));
+    if (!h->engine) {
+        cudaStream_t s;
+        CU(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        int rc = ieti_engine_create(s, &h->engine);
+        if (rc != IETIDP_OK) {
+            cudaStreamDestroy(s);
+            return rc;
+        }
+        h->engine->own_stream = true;
+    }
     *E = h->engine;
     return IETIDP_OK;
 }
@@ -759,8 +913,12 @@ int run_jobs(ietidp_handle* const* hs, int n, std::vector<EngineJob>& jobs, bool
     auto cleanup = [&]() {
         for (auto ev : evs) cudaEventDestroy(ev);
     };
-    for (int i = 1; i < n; ++i) {
+    // the engine's stream waits for work queued on every handle's stream
+    for (int i = 0; i < n; ++i) {
         if (hs[i]->st == st) continue;
+        bool dup = false;
+        for (int k = 0; k < i; ++k) dup = dup || hs[k]->st == hs[i]->st;
+        if (dup) continue;
         cudaEvent_t ev;
         CU(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
         evs.push_back(ev);
@@ -802,11 +960,11 @@ int run_jobs(ietidp_handle* const* hs, int n, std::vector<EngineJob>& jobs, bool
             if (e != cudaSuccess) rc = fail(IETIDP_E_CUDA, cudaGetErrorString(e));
         }
     }
-    // later work on the other handles' streams waits for the batch
+    // later work on the handles' streams waits for the batch
     if (!evs.empty()) {
         cudaEvent_t done = evs[0];
         cudaEventRecord(done, st);
-        for (int i = 1; i < n; ++i)
+        for (int i = 0; i < n; ++i)
             if (hs[i]->st != st) cudaStreamWaitEvent(hs[i]->st, done, 0);
     }
     cleanup();

@@ -80,13 +80,13 @@ __global__ void k_project_kerC(int nrows, const PatchDesc* pd, const int* crow_p
     for (int e = crow_ptr[row] + lane; e < crow_ptr[row + 1]; e += 32) v[c_idx[e]] -= c_w[e] * c;
 }
 
-// out^(k) = w^(k) + sum_j Phi^(k)_j u_Pi[A^(k)(j)], one CTA per patch
+// out^(k) = w^(k) + sum_j Phi^(k)_j u_Pi[A^(k)(j)]; blockIdx.y = patch
 __global__ void k_function(const PatchDesc* pd, const int* crow_glob, const double* phi, const double* uP,
                            const double* w, double* out) {
-    const PatchDesc& P = pd[blockIdx.x];
+    const PatchDesc& P = pd[blockIdx.y];
     const int n = P.n;
     const double* ph = phi + P.phioff;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         double s = w[P.toff + i];
         for (int j = 0; j < P.npi; ++j) s += ph[(long long)j * n + i] * uP[crow_glob[P.crow0 + j]];
         out[P.toff + i] = s;
@@ -200,7 +200,7 @@ cudaError_t launch_project_kerC(int nrows, const PatchDesc* pd, const int* crow_
 
 cudaError_t launch_function(int npatch, const PatchDesc* pd, const int* crow_glob, const double* phi,
                             const double* uP, const double* w, double* out, cudaStream_t st) {
-    k_function<<<npatch, 256, 0, st>>>(pd, crow_glob, phi, uP, w, out);
+    k_function<<<dim3(32, npatch), 256, 0, st>>>(pd, crow_glob, phi, uP, w, out);
     return cudaGetLastError();
 }
 
