@@ -128,6 +128,12 @@ typedef struct ietidp_handle ietidp_handle;
 #define IETIDP_METHOD_DUAL   0
 #define IETIDP_METHOD_SADDLE 1
 
+/* Primal basis solver (Eq. 6): CG with the Schoeberl-Zulehner preconditioner
+ * on the saddle-point system (Sec. 3.2, the paper's choice), or CG on ker C
+ * with the Euclidean projection (null-space method). */
+#define IETIDP_BASIS_SZ        0
+#define IETIDP_BASIS_NULLSPACE 1
+
 typedef struct {
     unsigned primal;          /* IETIDP_PRIMAL_* bitmask                       */
     int    precision;         /* IETIDP_PREC_*                                 */
@@ -144,6 +150,7 @@ typedef struct {
     int    method;            /* IETIDP_METHOD_* (dual PCG, MG-MG)             */
     int    saddle_vcycles;    /* MG-MG-S: V-cycles in the K~ preconditioner (3) */
     double saddle_theta;      /* MG-MG-S: block scaling theta (0.9)            */
+    int    basis_method;      /* IETIDP_BASIS_* (Schoeberl-Zulehner CG)        */
 } ietidp_options;
 
 typedef struct {

@@ -59,7 +59,8 @@ struct PatchDesc {
     long long a0off[2];  // coarsest inverse (n0 x n0), hierarchy 0 (Neumann) / 1 (Dirichlet)
     int npi;             // primal constraint rows of this patch
     int crow0;           // first global C row of this patch
-    long long phioff;    // Phi (n x npi, column-major)
+    long long phioff;    // Phi (n x npi, column-major); also the offset of W = Khat^{-1} C^T (SZ basis)
+    long long szhoff;    // Hhat^{-1} of the SZ basis solver (npi x npi, row-major)
     LevelDesc lev[IETI_MAXLEV];
 };
 

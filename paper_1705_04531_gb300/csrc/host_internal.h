@@ -128,6 +128,8 @@ struct ietidp_handle {
         *crow_glob = nullptr, *gptr = nullptr, *glist = nullptr;
     double* c_w = nullptr;
     double* phi = nullptr;
+    double* szW = nullptr;        // SZ basis: Khat^{-1} C^T (layout of phi)
+    double* szHinv = nullptr;     // SZ basis: Hhat^{-1} per patch
     double* Linv = nullptr;
     std::vector<double> spp_host;
     double *rloc = nullptr, *upi = nullptr, *uloc = nullptr;

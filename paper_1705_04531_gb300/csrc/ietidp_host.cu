@@ -23,6 +23,9 @@
 #include "host_internal.h"
 #include "engine.h"
 
+// small vectors of one SZ basis slot (sz_device.cuh: kSmall)
+static constexpr long long ieti_sz_small() { return 64; }
+
 namespace ieti_host {
 thread_local std::string g_err;
 std::atomic<long long> g_kernel_launches{0};
@@ -77,6 +80,7 @@ extern "C" void ietidp_default_options(ietidp_options* o) {
     o->method = IETIDP_METHOD_DUAL;
     o->saddle_vcycles = 3;
     o->saddle_theta = 0.9;
+    o->basis_method = IETIDP_BASIS_SZ;
 }
 
 // ---------------------------------------------------------------------------
@@ -435,6 +439,8 @@ SolveArgs ieti_solve_args(const ietidp_handle* h, int mode, const double* in, do
     a.dbg = h->dbg;
     a.phase = h->phase;
     a.batch = nullptr;
+    a.szW = h->szW;
+    a.szHinv = h->szHinv;
     return a;
 }
 
@@ -516,7 +522,8 @@ extern "C" int ietidp_setup(const iga_problem* P, const ietidp_options* opt_in, 
         !(opt.tol_basis > 0) || opt.alpha_reg < 0)
         return fail(IETIDP_E_INVALID_ARG, "bad options");
     if ((opt.method != IETIDP_METHOD_DUAL && opt.method != IETIDP_METHOD_SADDLE) || opt.saddle_vcycles < 1 ||
-        !(opt.saddle_theta > 0 && opt.saddle_theta < 1))
+        !(opt.saddle_theta > 0 && opt.saddle_theta < 1) ||
+        (opt.basis_method != IETIDP_BASIS_SZ && opt.basis_method != IETIDP_BASIS_NULLSPACE))
         return fail(IETIDP_E_INVALID_ARG, "bad method options");
     auto t0 = std::chrono::steady_clock::now();
     auto* h = new ietidp_handle();
@@ -695,7 +702,7 @@ extern "C" int ietidp_setup(const iga_problem* P, const ietidp_options* opt_in, 
     }
     // ---- levels and descriptors ----------------------------------------------
     h->pd.resize(N);
-    long long koff = 0, toff_tab = 0, itoff = 0, a0off = 0, phioff = 0;
+    long long koff = 0, toff_tab = 0, itoff = 0, a0off = 0, phioff = 0, szhoff = 0;
     int max_n0 = 1, max_S = 1, max_rows_lev = 1, max_L = 1;
     std::vector<TableJob> tjobs, mjobs;
     long long cg_need = 0, lv_need = 0;
@@ -775,6 +782,8 @@ extern "C" int ietidp_setup(const iga_problem* P, const ietidp_options* opt_in, 
         q.crow0 = crow0[k];
         q.phioff = phioff;
         phioff += (long long)q.n * q.npi;
+        q.szhoff = szhoff;
+        szhoff += (long long)q.npi * q.npi;
         cg_need = std::max(cg_need, (long long)q.n);
         lv_need = std::max(lv_need, (long long)q.nlvec);
         if (toff_tab > (1LL << 31) - 1 || itoff > (1LL << 31) - 1) return bail(fail(IETIDP_E_INVALID_ARG, "tables too large"));
@@ -805,6 +814,11 @@ extern "C" int ietidp_setup(const iga_problem* P, const ietidp_options* opt_in, 
     CKH(h->mem.upload(&d_tang, crow_tang_v, st));
     CKH(h->mem.alloc(&h->c_w, (long long)c_idx.size()));
     CKH(h->mem.alloc(&h->phi, phioff));
+    const bool sz = opt.basis_method == IETIDP_BASIS_SZ;
+    if (sz) {
+        CKH(h->mem.alloc(&h->szW, phioff));
+        CKH(h->mem.alloc(&h->szHinv, szhoff));
+    }
     CKH(h->mem.alloc(&h->Linv, (long long)npi * npi));
     CKH(h->mem.alloc(&h->rloc, h->nrows));
     CKH(h->mem.alloc(&h->upi, npi));
@@ -924,7 +938,9 @@ extern "C" int ietidp_setup(const iga_problem* P, const ietidp_options* opt_in, 
             nl = (nl + 3) & ~3LL;
             cgo[s] = cg_total;
             lvo[s] = lv_total;
-            cg_total += 5 * n;
+            // Neumann / Schur / null-space basis slots: 5 n; SZ basis slots:
+            // 8 n + 8 x 64 (sz_device.cuh)
+            cg_total += (sz && s < nslot_basis) ? 8 * n + 8 * ieti_sz_small() : 5 * n;
             lv_total += nl;
         }
         for (int k = 0; k < N; ++k) sp[k] = SlotDesc{k, 0, 0, k, 0, 0, cgo[k], lvo[k]};
@@ -960,7 +976,15 @@ extern "C" int ietidp_setup(const iga_problem* P, const ietidp_options* opt_in, 
     }
     // ---- primal basis (Eq. 6) ---------------------------------------------
     if (nslot_basis > 0) {
-        CHK(run_solve(h, MODE_BASIS, h->gbasis, nullptr, nullptr, opt.tol_basis, opt.maxit_inner, h->vst + 8));
+        if (sz) {
+            // W = Khat^{-1} C^T per constraint row, Hhat^{-1} per patch, then SZ-CG
+            CHK(run_solve(h, MODE_SZW, h->gbasis, nullptr, nullptr, 0.0, 0, h->vst + 8));
+            cudaError_t e = launch_sz_hinv(h->d_pd, N, h->crow_ptr, h->c_idx, h->c_w, h->szW, h->szHinv, h->flags, st);
+            if (e != cudaSuccess) return bail(fail(IETIDP_E_CUDA, std::string("SZ set-up: ") + cudaGetErrorString(e)));
+            CHK(run_solve(h, MODE_BASIS_SZ, h->gbasis, nullptr, nullptr, opt.tol_basis, opt.maxit_inner, h->vst + 8));
+        } else {
+            CHK(run_solve(h, MODE_BASIS, h->gbasis, nullptr, nullptr, opt.tol_basis, opt.maxit_inner, h->vst + 8));
+        }
         CUH(cudaStreamSynchronize(st));
         std::vector<int> its(nslot_basis);
         CUH(cudaMemcpyAsync(its.data(), h->its, sizeof(int) * nslot_basis, cudaMemcpyDeviceToHost, st));

@@ -58,6 +58,10 @@ cudaError_t launch_cweights(const PatchDesc* pd, int nrows, const int* crow_ptr,
 
 cudaError_t launch_to_f32(const double* src, float* dst, long long n, cudaStream_t st);
 
+// SZ basis: Hhat^{-1} = (0.99 C W)^{-1} per patch (W = Khat^{-1} C^T, layout of phi)
+cudaError_t launch_sz_hinv(const PatchDesc* pd, int npatch, const int* crow_ptr, const int* c_idx,
+                           const double* c_w, const double* szW, double* szHinv, int* flags, cudaStream_t st);
+
 // Dense SPD: Cholesky factor and inverse of the lower factor, one CTA.
 cudaError_t launch_chol_linv(const double* A, int n, double* Linv, double* work, int* flags,
                              cudaStream_t st);
@@ -79,7 +83,18 @@ struct SlotDesc {
 
 // MODE_POWER: V-cycle contraction estimate per patch (BPCG scaling);
 // MODE_KHAT: Delta block of the BPCG preconditioner, P V^ncycles P^T / omega
-enum SlotMode { MODE_NEUMANN = 0, MODE_BASIS = 1, MODE_SCHUR = 2, MODE_VCYCLE = 3, MODE_POWER = 4, MODE_KHAT = 5 };
+// MODE_SZW / MODE_BASIS_SZ: primal basis by Schoeberl-Zulehner CG (W = Khat^{-1} C^T
+// per constraint row, then one SZ-CG per constraint row)
+enum SlotMode {
+    MODE_NEUMANN = 0,
+    MODE_BASIS = 1,
+    MODE_SCHUR = 2,
+    MODE_VCYCLE = 3,
+    MODE_POWER = 4,
+    MODE_KHAT = 5,
+    MODE_SZW = 6,
+    MODE_BASIS_SZ = 7
+};
 
 struct SolveArgs {
     const PatchDesc* pd;
@@ -115,6 +130,8 @@ struct SolveArgs {
     int ncycles;               // Schur / K-hat: V-cycles; V-cycle mode: cycles
     double theta;              // power mode: omega_k = theta (1 - rho_k^ncycles)
     double* omega;             // per patch BPCG scaling (written by the power mode, read by K-hat)
+    double* szW;               // SZ basis: W = Khat^{-1} C^T pool (layout of phi)
+    const double* szHinv;      // SZ basis: Hhat^{-1} pool (PatchDesc::szhoff)
     long long* vstats;         // [0] V-cycles, [1] V-cycle fine dofs (atomically added)
     size_t smem_bytes;         // dynamic shared memory of the launch (specialised kernels)
     int* dbg;                  // self-check record (debug builds only)

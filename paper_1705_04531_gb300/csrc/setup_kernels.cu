@@ -773,3 +773,76 @@ cudaError_t launch_chol_linv(const double* A, int n, double* Linv, double* work,
     k_chol_linv<<<1, 512, 0, st>>>(work, n, Linv, flags);
     return cudaGetLastError();
 }
+
+// ---------------------------------------------------------------------------
+// SZ basis: Hhat^{-1} = (0.99 H)^{-1}, H = C W with W = Khat^{-1} C^T (Sec. 3.2),
+// one CTA per patch; Gauss-Jordan on the symmetrised SPD matrix (n_Pi^(k) <=
+// 64) in dynamic shared memory (2 npi^2 doubles)
+// ---------------------------------------------------------------------------
+__global__ void k_sz_hinv(const PatchDesc* pd, const int* crow_ptr, const int* c_idx, const double* c_w,
+                          const double* szW, double* szHinv, int* flags) {
+    extern __shared__ double shm_sz[];
+    const PatchDesc& P = pd[blockIdx.x];
+    const int npi = P.npi, n = P.n;
+    if (npi == 0) return;
+    double* A = shm_sz;
+    double* B = shm_sz + npi * npi;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const double* W = szW + P.phioff;
+    for (int pr = w; pr < npi * npi; pr += nw) {
+        const int i = pr / npi, j = pr % npi;
+        const int row = P.crow0 + i;
+        double d = 0.0;
+        for (int e = crow_ptr[row] + lane; e < crow_ptr[row + 1]; e += 32) d += c_w[e] * W[(long long)j * n + c_idx[e]];
+        for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+        if (lane == 0) A[pr] = d;
+    }
+    __syncthreads();
+    for (int pr = threadIdx.x; pr < npi * npi; pr += blockDim.x) {
+        const int i = pr / npi, j = pr % npi;
+        B[pr] = 0.99 * 0.5 * (A[pr] + A[j * npi + i]);
+    }
+    __syncthreads();
+    for (int pr = threadIdx.x; pr < npi * npi; pr += blockDim.x) {
+        A[pr] = B[pr];
+        B[pr] = (pr / npi == pr % npi) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    for (int k = 0; k < npi; ++k) {
+        const double piv = A[k * npi + k];
+        if (!(piv > 0.0)) {
+            if (threadIdx.x == 0) atomicOr(flags, IETI_FLAG_NOT_SPD);
+            return;
+        }
+        __syncthreads();
+        for (int c = threadIdx.x; c < npi; c += blockDim.x) {
+            A[k * npi + c] /= piv;
+            B[k * npi + c] /= piv;
+        }
+        __syncthreads();
+        for (int pr = threadIdx.x; pr < npi * npi; pr += blockDim.x) {
+            const int i = pr / npi, c = pr % npi;
+            if (i == k) continue;
+            const double f = A[i * npi + k];
+            // column k of A is read by every row update: take it before it changes
+            A[i * npi + c] -= (c == k ? 0.0 : f * A[k * npi + c]);
+            B[i * npi + c] -= f * B[k * npi + c];
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < npi; i += blockDim.x)
+            if (i != k) A[i * npi + k] = 0.0;
+        __syncthreads();
+    }
+    double* out = szHinv + P.szhoff;
+    for (int pr = threadIdx.x; pr < npi * npi; pr += blockDim.x) out[pr] = B[pr];
+}
+
+cudaError_t launch_sz_hinv(const PatchDesc* pd, int npatch, const int* crow_ptr, const int* c_idx,
+                           const double* c_w, const double* szW, double* szHinv, int* flags, cudaStream_t st) {
+    if (npatch == 0) return cudaSuccess;
+    const size_t sm = sizeof(double) * 2 * 64 * 64;
+    cudaError_t e = cudaFuncSetAttribute(k_sz_hinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_sz_hinv<<<npatch, 256, sm, st>>>(pd, crow_ptr, c_idx, c_w, szW, szHinv, flags);
+    return cudaGetLastError();
+}

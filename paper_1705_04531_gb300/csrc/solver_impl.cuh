@@ -12,11 +12,14 @@
 //
 // Modes (Sec. 3): Neumann solve inside F and K~^{-1} (CG on K, V-cycle on K
 // or K + alpha M^, right-hand side P^T g, result P z + Phi u_Pi), primal basis
-// (Eq. 6 by the null-space method), scaled-Dirichlet Schur application
-// (two V-cycles on K_II), and a plain V-cycle iteration for benchmarking.
+// (Eq. 6 by the null-space method, or by Schoeberl-Zulehner CG: sz_device.cuh),
+// scaled-Dirichlet Schur application (two V-cycles on K_II), the MG-MG-S
+// blocks (contraction estimate, K-hat), and a plain V-cycle iteration for
+// benchmarking.
 #pragma once
 #include <math.h>
 #include "kernels.cuh"
+#include "sz_device.cuh"
 
 namespace ieti_t {
 
@@ -836,6 +839,32 @@ __global__ void __launch_bounds__(512) k_solve_t(SolveArgs a0) {
         if (threadIdx.x == 0 && a.vstats) {
             atomicAdd((unsigned long long*)&a.vstats[0], (unsigned long long)vcount);
             atomicAdd((unsigned long long*)&a.vstats[1], (unsigned long long)(vcount * n));
+        }
+        return;
+    }
+
+    if (a.mode == MODE_SZW || a.mode == MODE_BASIS_SZ) {
+        auto vcyc = [&](const double* in, double* out) {
+            vcycle_apply(vc, in, out, a.nu1, a.nu2);
+            ++vcount;
+        };
+        auto spk = [&](const double* in, double* out) {
+            spmv64<D, P0, P1, P2>(P, a.K64, in, out, P.dmask, nullptr, 1.0, 0);
+        };
+        double* base = a.cg + sd.cg;
+        int it = 0;
+        bool conv = true;
+        if (a.mode == MODE_SZW) ieti_sz::szw_slot(a, P, sd, base, vcyc);
+        else it = ieti_sz::sz_basis_slot(a, P, sd, base, &red.v[0][0], coef, vcyc, spk, &conv);
+        if (threadIdx.x == 0) {
+            if (a.mode == MODE_BASIS_SZ) {
+                a.its[sd.its] = it;
+                if (!conv) atomicOr(a.flags, IETI_FLAG_NOT_CONVERGED);
+            }
+            if (a.vstats) {
+                atomicAdd((unsigned long long*)&a.vstats[0], (unsigned long long)vcount);
+                atomicAdd((unsigned long long*)&a.vstats[1], (unsigned long long)(vcount * n));
+            }
         }
         return;
     }

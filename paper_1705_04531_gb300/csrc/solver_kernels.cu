@@ -10,6 +10,7 @@
 // solve) runs in T = double or T = float.
 #include <math.h>
 #include "kernels.cuh"
+#include "sz_device.cuh"
 
 namespace {
 
@@ -448,6 +449,36 @@ __global__ void __launch_bounds__(512) k_solve(SolveArgs a0) {
         if (threadIdx.x == 0 && a.vstats) {
             atomicAdd((unsigned long long*)&a.vstats[0], (unsigned long long)vcount);
             atomicAdd((unsigned long long*)&a.vstats[1], (unsigned long long)(vcount * n));
+        }
+        return;
+    }
+
+    if (a.mode == MODE_SZW || a.mode == MODE_BASIS_SZ) {
+        auto vcyc = [&](const double* in, double* out) {
+            vcycle_apply(vc, in, out, a.nu1, a.nu2);
+            ++vcount;
+        };
+        auto spk = [&](const double* in, double* out) {
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                int i0 = i % F.m[0], i1 = (i / F.m[0]) % F.m[1], i2 = i / (F.m[0] * F.m[1]);
+                out[i] = ieti_masked(P.dmask, F.m, i0, i1, i2) ? 0.0 : k64_row(P, a.K64, in, i);
+            }
+            __syncthreads();
+        };
+        double* base = a.cg + sd.cg;
+        int it = 0;
+        bool conv = true;
+        if (a.mode == MODE_SZW) ieti_sz::szw_slot(a, P, sd, base, vcyc);
+        else it = ieti_sz::sz_basis_slot(a, P, sd, base, &red.v[0][0], coef, vcyc, spk, &conv);
+        if (threadIdx.x == 0) {
+            if (a.mode == MODE_BASIS_SZ) {
+                a.its[sd.its] = it;
+                if (!conv) atomicOr(a.flags, IETI_FLAG_NOT_CONVERGED);
+            }
+            if (a.vstats) {
+                atomicAdd((unsigned long long*)&a.vstats[0], (unsigned long long)vcount);
+                atomicAdd((unsigned long long*)&a.vstats[1], (unsigned long long)(vcount * n));
+            }
         }
         return;
     }

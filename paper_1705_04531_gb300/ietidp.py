@@ -33,6 +33,7 @@ RHS = {"none": 0, "sin2d": 1, "sin3d": 2, "annulus": 3, "modes": 4, "quad": 5}
 PRIMAL = {"vertex": 1, "edge": 2, "face": 4}
 PREC_FP64, PREC_MIXED = 0, 1
 METHOD = {"dual": 0, "saddle": 1}
+BASIS = {"sz": 0, "nullspace": 1}
 
 
 class iga_patch_desc(C.Structure):
@@ -59,7 +60,7 @@ class ietidp_options(C.Structure):
                 ("maxit_inner", C.c_int), ("nu_pre", C.c_int), ("nu_post", C.c_int),
                 ("coarse_elems", C.c_int), ("dirichlet_vcycles", C.c_int), ("alpha_reg", C.c_double),
                 ("cluster", C.c_int), ("method", C.c_int), ("saddle_vcycles", C.c_int),
-                ("saddle_theta", C.c_double)]
+                ("saddle_theta", C.c_double), ("basis_method", C.c_int)]
 
 
 class ietidp_stats(C.Structure):
@@ -213,6 +214,8 @@ def default_options(**kw) -> ietidp_options:
             v = PREC_MIXED if v == "mixed" else PREC_FP64
         if k == "method" and isinstance(v, str):
             v = METHOD[v]
+        if k == "basis_method" and isinstance(v, str):
+            v = BASIS[v]
         setattr(o, k, v)
     return o
 

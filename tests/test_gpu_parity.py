@@ -86,11 +86,22 @@ def test_assembly(api, name):
         assert np.abs(got[k] - ref[k]).max() <= 1e-12 * np.abs(ref[k]).max()
 
 
-def test_primal_basis_and_coarse_matrix(api):
-    dom = DOMS["annulus3x3"]()
+@pytest.mark.parametrize("name", ["annulus3x3", "cube_rq", "uneven3x3"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("basis", ["sz", "nullspace"])
+def test_primal_basis_and_coarse_matrix(api, name, prec, basis):
+    """Primal basis by Schoeberl-Zulehner CG (default) and by the null-space
+    CG, both against the direct solution of Eq. 6; SZ-CG iterations against
+    the oracle's SZ-CG."""
+    dom = DOMS[name]()
     orc = O.IETIDP(dom, O.Options(mode="direct"))
     prob = api.Problem(dom)
-    sol = api.Solver(prob)
+    sol = api.Solver(prob, precision=prec, basis_method=basis)
+    st = sol.solve()[1]
+    if basis == "sz" and prec == "fp64":
+        from oracle import szcg
+        _, its = szcg.sz_basis(O.IETIDP(dom, O.Options(mode="mg")))
+        assert abs(st["basis_it_avg"] - np.mean(its)) <= 1.0, (st["basis_it_avg"], np.mean(its))
     for k in range(dom.npatch):
         phi = sol.primal_basis(k).cpu().numpy()          # (npi_k, n_full)
         ref = np.zeros((orc.phi[k].shape[1], phi.shape[1]))
