@@ -75,7 +75,11 @@ class SZPatch:
 
 
 def sz_basis_column(pz: SZPatch, j, tol, maxit):
-    """phi_j by SZ-preconditioned CG.  Returns (phi_j, iterations, converged)."""
+    """phi_j by SZ-preconditioned CG.  Returns (phi_j, iterations, converged).
+
+    The recursively updated residuals drift by rounding (r.rt - r.(A r) is a
+    difference of close numbers at tol_basis = 1e-12), so the iteration
+    restarts from the residual b - A x after every 1e-4 of reduction."""
     n, npi = pz.W.shape
     b1, b2 = np.zeros(n), np.zeros(npi)
     b2[j] = 1.0
@@ -85,6 +89,8 @@ def sz_basis_column(pz: SZPatch, j, tol, maxit):
     Ar1, Ar2 = pz.saddle(r1, r2)
     rho = r1 @ rt1 + r2 @ rt2 - (r1 @ Ar1 + r2 @ Ar2)
     rho0 = rho
+    rho_cycle = rho
+    restarts = 0
     p1, p2, Ap1, Ap2 = r1.copy(), r2.copy(), Ar1.copy(), Ar2.copy()
     for it in range(1, maxit + 1):
         q1, q2 = pz.precond(Ap1, Ap2)
@@ -102,8 +108,20 @@ def sz_basis_column(pz: SZPatch, j, tol, maxit):
         Ar1 -= alpha * Aq1
         Ar2 -= alpha * Aq2
         rho_new = r1 @ rt1 + r2 @ rt2 - (r1 @ Ar1 + r2 @ Ar2)
-        if rho_new <= tol * tol * rho0:
+        if 0.0 <= rho_new <= tol * tol * rho0:
             return x1, it, True
+        if (rho_new <= 1e-8 * rho_cycle or rho_new < 0.0) and restarts < 20:
+            restarts += 1
+            t1, t2 = pz.saddle(x1, x2)
+            rt1, rt2 = b1 - t1, b2 - t2
+            r1, r2 = pz.precond(rt1, rt2)
+            Ar1, Ar2 = pz.saddle(r1, r2)
+            rho = r1 @ rt1 + r2 @ rt2 - (r1 @ Ar1 + r2 @ Ar2)
+            rho_cycle = rho
+            if rho <= tol * tol * rho0:
+                return x1, it, True
+            p1, p2, Ap1, Ap2 = r1.copy(), r2.copy(), Ar1.copy(), Ar2.copy()
+            continue
         beta = rho_new / rho
         rho = rho_new
         p1 = r1 + beta * p1

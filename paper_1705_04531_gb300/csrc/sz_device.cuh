@@ -8,9 +8,9 @@
 // precomputed per patch (modes SZW and the per-patch inverse kernel).  CG runs
 // in the inner product of D = P - [K C^T; C 0], positive definite when
 // Khat > K and Hhat < C Khat^{-1} C^T; <r, r>_D = r.rt - r.(A r) with rt the
-// unpreconditioned residual.  One V-cycle and one K product per step.  With
-// FP32 V-cycles the iteration restarts from the FP64 residual after every
-// 1e-4 of reduction (the recursions drift by the FP32 rounding).
+// unpreconditioned residual.  One V-cycle and one K product per step.  The
+// iteration restarts from the FP64 residual after every 1e-4 of reduction
+// (the recursions drift by the rounding of the preconditioner).
 #pragma once
 #include "kernels.cuh"
 
@@ -184,9 +184,10 @@ __device__ int sz_basis_slot(const SolveArgs& a, const PatchDesc& P, const SlotD
     *conv = !(rho0 > 0.0);
     int it = 0;
     const double tol2 = a.tol * a.tol;
-    // FP32 V-cycles: the recursively updated residuals drift by their
-    // rounding, so the iteration restarts from the FP64 residual b - A x after
-    // every 1e-4 of reduction (iterative refinement)
+    // the recursively updated residuals drift by the rounding of the
+    // preconditioner (FP32 V-cycles, and the cancellation in
+    // r.rt - r.(A r) in FP64 at tol_basis = 1e-12), so the iteration restarts
+    // from the FP64 residual b - A x after every 1e-4 of reduction
     double rho_cycle = rho0;
     int restarts = 0;
     while (!*conv && it < a.maxit) {
@@ -221,7 +222,7 @@ __device__ int sz_basis_slot(const SolveArgs& a, const PatchDesc& P, const SlotD
             *conv = true;
             break;
         }
-        if (a.mixed && (rho_new <= 1e-8 * rho_cycle || rho_new < 0.0) && restarts < 20) {
+        if ((rho_new <= 1e-8 * rho_cycle || rho_new < 0.0) && restarts < 20) {
             ++restarts;
             saddle(x1, x2, t1, t2);
             for (int i = threadIdx.x; i < n; i += blockDim.x) rt1[i] = -t1[i];
