@@ -517,10 +517,13 @@ def main():
 
     peak, peak_kind = peaks()
     traffic = None
-    tp = os.path.join(ROOT, "profiles", "traffic.json")
+    tp = os.path.join(ROOT, "profiles", "traffic.txt")
     if os.path.exists(tp):
         with open(tp) as fh_:
-            traffic = json.load(fh_).get(args.workload)
+            for ln in fh_:
+                f_ = ln.split()
+                if len(f_) == 2 and not ln.startswith("#") and f_[0] == args.workload:
+                    traffic = float(f_[1])
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
