@@ -230,6 +230,22 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(x, dist, device):
+    """Largest value of x over the ranks (x itself without a process group)."""
+    if not dist:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(max_ms, world, batch, steps):
+    """Whole-job throughput: every rank solves `batch` copies per step (weak
+    scaling, independent replicas); time = the slowest rank's."""
+    return world * batch * steps / (max_ms / 1e3)
+
+
 def time_path(api, torch, prob, prec, args, flush, stream):
     t0 = time.perf_counter()
     sol = api.Solver(prob, precision=prec)
@@ -467,12 +483,8 @@ def main():
     with Clocks(local) as clk:
         bt = time_batch(api, torch, dom, "mixed", args, flush, stream)
     ms = bt["ms"]
-    tot = sum(ms)
-    if dist:
-        t = torch.tensor([tot], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot = float(t.item())
-    value = world * args.batch * args.steps / (tot / 1e3)
+    tot = max_over_ranks(sum(ms), dist, "cuda")
+    value = job_value(tot, world, args.batch, args.steps)
     ub = [bt["sols"][i].split(bt["us"][i]) for i in range(args.batch)]
 
     # e2e through the C ABI with host buffers (pinned), copies inside the timed region

@@ -1,7 +1,8 @@
 """Full-size workloads on the GPU, in the configuration bench.py times.
 
 * quarter annulus 6x6, p=3, 64x64 elements per patch: the whole solution
-  against the oracle's conforming direct solve (rel. error <= 1e-8);
+  against the oracle's conforming direct solve (rel. error <= 1e-8), alone
+  and as the benchmark's batch of 8 copies (MG-MG and MG-MG-S);
 * uneven 8x8 batch (degrees 2..4, 32..256 elements per direction) and the
   2x2x2 cube (p=2, 32^3 elements per patch): too large for the oracle's
   global solve, so sampled rows are checked one by one -- the oracle
@@ -71,6 +72,32 @@ def test_annulus_full_size(api, prec):
     ref = mp.to_patches(mp.solve_global())
     err = np.sqrt(sum(np.sum((a - b) ** 2) for a, b in zip(got, ref)) / sum(np.sum(b ** 2) for b in ref))
     assert st["converged"] and err <= 1e-8, err
+
+
+@pytest.fixture(scope="module")
+def annulus_ref():
+    dom = W.annulus_6x6(64, 3)
+    mp = Multipatch(dom)
+    return dom, mp.to_patches(mp.solve_global())
+
+
+@pytest.mark.parametrize("method", ["dual", "saddle"])
+def test_annulus_batch_of_8_as_benchmarked(api, annulus_ref, method):
+    """The benchmark's step: 8 copies of the annulus in one lockstep batch
+    (mixed; the tuned 256-thread, 2-CTA-per-SM launches), every copy against
+    the direct solve; MG-MG and MG-MG-S."""
+    dom, ref = annulus_ref
+    probs = [api.Problem(dom) for _ in range(8)]
+    sols = [api.Solver(p, precision="mixed", method=method) for p in probs]
+    us, sts = api.Solver.solve_batch(sols)
+    for s_, u, st in zip(sols, us, sts):
+        got = s_.split(u)
+        err = np.sqrt(sum(np.sum((a - b) ** 2) for a, b in zip(got, ref)) / sum(np.sum(b ** 2) for b in ref))
+        assert st["converged"] and err <= 1e-8, (err, st["outer_it"])
+    for s_ in sols:
+        s_.close()
+    for p in probs:
+        p.close()
 
 
 @pytest.mark.parametrize("name", ["uneven8x8", "cube2x2x2"])
