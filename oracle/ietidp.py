@@ -1,5 +1,5 @@
-"""IETI-DP with energy-minimizing primal subspace, D-D and MG-MG variants
-(Sec. 2-4 of the paper).
+"""IETI-DP with energy-minimizing primal subspace, D-D, D-MG and MG-MG
+variants (Sec. 2-4 of the paper).
 
 ORACLE (test infrastructure only).  Plain FP64 numpy/scipy, one patch at a
 time, in the order the paper states the algorithm.
@@ -35,7 +35,9 @@ each row), local part of the jump operator B.
   constants, which P removes).
 * F = B K~^{-1} B^T, d = B K~^{-1} f (Eq. 4); scaled Dirichlet preconditioner
   M_sD^{-1} = B_D S B_D^T with S = K_BB - K_BI K_II^{-1} K_IB; K_II^{-1} exact
-  (D-D) or two V-cycles (MG-MG, Sec. 4).
+  (D-D) or two V-cycles (MG-MG and D-MG, Sec. 4).  D-MG: the Neumann problems
+  (F, d, recovery) and the primal basis by the saddle LU, the Dirichlet
+  problems of the preconditioner by multigrid (Sec. 3.3).
 * Outer CG on F lambda = d, lambda_0 = 0, stop at ||r|| <= tol ||d||
   (Sec. 4), then u = K~^{-1}(f - B^T lambda).  The condition number is
   estimated from the CG coefficients (Lanczos tridiagonal).
@@ -61,7 +63,7 @@ from .domain import Multipatch
 
 @dataclass
 class Options:
-    mode: str = "direct"          # "direct" (D-D) or "mg" (MG-MG)
+    mode: str = "direct"          # "direct" (D-D), "mg" (MG-MG) or "dmg" (D-MG)
     tol_outer: float = 1e-10
     tol_inner: float = 1e-12      # Neumann solves in F, d and the recovery
     tol_basis: float = 1e-12      # primal basis
@@ -131,6 +133,11 @@ class IETIDP:
         self._build_jump()
         if self.o.mode == "direct":
             self._setup_direct()
+        elif self.o.mode == "dmg":
+            # D-MG (Sec. 3.3): direct local Neumann solves and primal basis,
+            # multigrid for the Dirichlet problems of the preconditioner
+            self._setup_direct()
+            self._setup_mg_dirichlet()
         else:
             self._setup_mg()
         self._setup_coarse()
@@ -292,6 +299,16 @@ class IETIDP:
             self.mgD.append(multigrid.MGOperator(h, allsides, 0.0, o.nu1, o.nu2))
             self.phi.append(self._basis_mg(k))
 
+    def _setup_mg_dirichlet(self):
+        o = self.o
+        self.hier, self.mgD = [], []
+        d = self.dom.dim
+        allsides = (1 << (2 * d)) - 1
+        for k in range(self.N):
+            h = multigrid.Hierarchy(self.Kfull[k], self.dom.patch_nelem(k), self.dom.patch_degree(k), o.cmin)
+            self.hier.append(h)
+            self.mgD.append(multigrid.MGOperator(h, allsides, 0.0, o.nu1, o.nu2))
+
     def _projector(self, k):
         C = self.C[k]
         Cd = C.toarray()
@@ -335,7 +352,7 @@ class IETIDP:
         """Minimizer of 1/2 w'Kw - w'g over ker C (Eq. 7)."""
         C, phi = self.C[k], self.phi[k]
         npi = C.shape[0]
-        if self.o.mode == "direct":
+        if self.o.mode in ("direct", "dmg"):
             if npi == 0:
                 return self.kkt[k].solve(g)
             rhs = np.concatenate([g, np.zeros(npi)])

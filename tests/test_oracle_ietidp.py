@@ -1,5 +1,5 @@
 """Pins of the IETI-DP oracle (Sec. 2-4): its solution equals the conforming
-global direct solve, jumps vanish, the primal basis solves Eq. 6, MG-MG
+global direct solve in all three modes (D-D, D-MG, MG-MG), jumps vanish, the primal basis solves Eq. 6, MG-MG
 equals D-D, the Lanczos condition estimate equals the spectrum of the
 preconditioned dual operator, and kappa grows like (1 + log(H/h))^2."""
 import numpy as np
@@ -22,7 +22,7 @@ def _relerr(u, ref):
                    / sum(np.sum(b ** 2) for b in ref))
 
 
-@pytest.mark.parametrize("mode", ["direct", "mg"])
+@pytest.mark.parametrize("mode", ["direct", "mg", "dmg"])
 @pytest.mark.parametrize("case", range(len(CASES)))
 def test_equals_global_solve(case, mode):
     dom = CASES[case]()
@@ -119,3 +119,16 @@ def test_single_patch_has_no_multipliers():
     assert s.nlam == 0 and s.nPi == 0
     mp = Multipatch(dom)
     assert _relerr(u, mp.to_patches(mp.solve_global())) < 1e-11
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_dmg_iterations_equal_mgmg(case):
+    """D-MG and MG-MG share the preconditioner (Dirichlet problems by
+    multigrid); their Neumann solves differ only by the inner tolerance, so
+    the outer iteration counts agree to within one."""
+    dom = CASES[case]()
+    a = ietidp.IETIDP(dom, ietidp.Options(mode="dmg"))
+    a.solve()
+    b = ietidp.IETIDP(dom, ietidp.Options(mode="mg"))
+    b.solve()
+    assert abs(a.stats.outer_it - b.stats.outer_it) <= 1
