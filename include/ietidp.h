@@ -122,11 +122,15 @@ typedef struct iga_problem   iga_problem;
 typedef struct ietidp_handle ietidp_handle;
 
 /* Outer method (Sec. 3.3): dual PCG on F lambda = d with accurate local
- * Neumann solves (MG-MG), or Bramble-Pasciak CG on the saddle-point system
- * of Eq. 2 with a fixed number of V-cycles in the preconditioner of K~
+ * Neumann solves by multigrid-preconditioned CG (MG-MG) or by a direct
+ * banded solver (D-MG), or Bramble-Pasciak CG on the saddle-point system of
+ * Eq. 2 with a fixed number of V-cycles in the preconditioner of K~
  * (MG-MG-S). */
 #define IETIDP_METHOD_DUAL   0
 #define IETIDP_METHOD_SADDLE 1
+/* D-MG (Sec. 3.3): dual PCG with direct local Neumann solves (banded
+ * Cholesky of the fine K per patch) and multigrid Dirichlet problems */
+#define IETIDP_METHOD_DMG    2
 
 /* Primal basis solver (Eq. 6): CG with the Schoeberl-Zulehner preconditioner
  * on the saddle-point system (Sec. 3.2, the paper's choice), or CG on ker C

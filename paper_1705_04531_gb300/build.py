@@ -15,7 +15,7 @@ SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libietidp.so")
 SOURCES = ["setup_kernels.cu", "solver_kernels.cu", "dual_kernels.cu", "ietidp_host.cu", "ietidp_engine.cu",
-           "ietidp_saddle.cu", "saddle_kernels.cu",
+           "ietidp_saddle.cu", "saddle_kernels.cu", "direct_kernels.cu",
            "ietidp_server.cu",
            "solver_dispatch.cu"] + sorted(f for f in os.listdir(SRC) if f.startswith("solver_t_"))
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

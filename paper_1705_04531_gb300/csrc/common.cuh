@@ -61,6 +61,9 @@ struct PatchDesc {
     int crow0;           // first global C row of this patch
     long long phioff;    // Phi (n x npi, column-major); also the offset of W = Khat^{-1} C^T (SZ basis)
     long long szhoff;    // Hhat^{-1} of the SZ basis solver (npi x npi, row-major)
+    long long bandoff;   // D-MG: banded Cholesky factor of the fine K (n x (bw+1), by columns)
+    int bw;              // D-MG: half band width p0 + m0 (p1 + m1 p2)
+    int pin;             // D-MG: pinned dof of a floating patch (-1: none)
     LevelDesc lev[IETI_MAXLEV];
 };
 

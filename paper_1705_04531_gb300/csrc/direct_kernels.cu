@@ -1,0 +1,305 @@
+// D-MG (Sec. 3.3): direct local Neumann solves by banded Cholesky.
+//
+// Per patch, the fine-level stiffness K in the natural (lexicographic) order
+// of its full tensor grid is a band matrix of half-width
+// bw = p0 + m0 (p1 + m1 p2).  Rows and columns of functions on the Dirichlet
+// boundary become identity rows (their entries of every vector stay 0).  On a
+// patch without Dirichlet side K is singular (constants); one interior dof is
+// pinned (identity row and column): for a right-hand side orthogonal to the
+// constants -- P^T g is -- the pinned system gives one solution of K z = P^T g,
+// and the energy projection P removes the constant in which the solutions
+// differ (Sec. 3.2: w = P z).  The band is stored by columns, lower part:
+// band[bandoff + j (bw+1) + (i - j)] = L(i, j) for j <= i <= j + bw.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "kernels.cuh"
+
+namespace {
+
+// natural index of the pinned dof of a floating patch (-1: none)
+__device__ __forceinline__ bool pinned_or_masked(const PatchDesc& P, int i) {
+    const LevelDesc& L = P.lev[P.L - 1];
+    const int i0 = i % L.m[0], i1 = (i / L.m[0]) % L.m[1], i2 = i / (L.m[0] * L.m[1]);
+    return i == P.pin || ieti_masked(P.dmask, L.m, i0, i1, i2);
+}
+
+// band of K (lower part) from the color-blocked values; one CTA row-block per
+// (rows, patch)
+__global__ void k_band_assemble(const PatchDesc* pd, const int* plist, const double* K64, double* band) {
+    const PatchDesc& P = pd[plist[blockIdx.y]];
+    const LevelDesc& L = P.lev[P.L - 1];
+    const int bw = P.bw;
+    double* B = band + P.bandoff;
+    const int W0 = 2 * P.p[0] + 1, W1 = 2 * P.p[1] + 1;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < L.n; i += gridDim.x * blockDim.x) {
+        const int i0 = i % L.m[0], i1 = (i / L.m[0]) % L.m[1], i2 = i / (L.m[0] * L.m[1]);
+        const bool fixed = pinned_or_masked(P, i);
+        for (int o2 = -P.p[2]; o2 <= P.p[2]; ++o2)
+            for (int o1 = -P.p[1]; o1 <= P.p[1]; ++o1)
+                for (int o0 = -P.p[0]; o0 <= P.p[0]; ++o0) {
+                    const int d = o0 + L.m[0] * (o1 + L.m[1] * o2);
+                    if (d > 0) continue;   // lower part: column j = i + d <= i
+                    const int j0 = i0 + o0, j1 = i1 + o1, j2 = i2 + o2;
+                    if (j0 < 0 || j0 >= L.m[0] || j1 < 0 || j1 >= L.m[1] || j2 < 0 || j2 >= L.m[2]) continue;
+                    const int j = i + d;
+                    double v;
+                    if (d == 0) {
+                        v = fixed ? 1.0 : K64[L.koff + ieti_val_pos(L.m, P.p, L.S, i0, i1, i2,
+                                                                        (o0 + P.p[0]) + W0 * ((o1 + P.p[1]) + W1 * (o2 + P.p[2])))];
+                    } else {
+                        v = (fixed || pinned_or_masked(P, j))
+                                ? 0.0
+                                : K64[L.koff + ieti_val_pos(L.m, P.p, L.S, i0, i1, i2,
+                                                            (o0 + P.p[0]) + W0 * ((o1 + P.p[1]) + W1 * (o2 + P.p[2])))];
+                    }
+                    B[(long long)j * (bw + 1) + (i - j)] = v;
+                }
+    }
+}
+
+// right-looking band Cholesky, one CTA per patch: column j is scaled and
+// kept in shared memory, then every row l of the trailing window subtracts
+// L(j+l, j) L(j+k, j) from A(j+l, j+k), k <= l; a thread owns a row l and
+// reads/writes 16 of its entries per batch (loads issued together), lanes of
+// a warp own consecutive rows (coalesced per k)
+__global__ void k_band_cholesky(const PatchDesc* pd, const int* plist, double* band, int* flags) {
+    extern __shared__ double colj[];
+    __shared__ int bad;
+    const PatchDesc& P = pd[plist[blockIdx.x]];
+    const int n = P.n, bw = P.bw;
+    double* B = band + P.bandoff;
+    if (threadIdx.x == 0) bad = 0;
+    __syncthreads();
+    for (int j = 0; j < n; ++j) {
+        double* cj = B + (long long)j * (bw + 1);
+        const int w = min(bw, n - 1 - j);
+        if (threadIdx.x == 0) {
+            const double a = cj[0];
+            if (!(a > 0.0)) bad = 1;
+            const double d = a > 0.0 ? sqrt(a) : 1.0;
+            cj[0] = d;
+            colj[0] = d;
+        }
+        __syncthreads();
+        if (bad) break;
+        const double inv = 1.0 / colj[0];
+        for (int t = 1 + threadIdx.x; t <= w; t += blockDim.x) {
+            const double v = cj[t] * inv;
+            cj[t] = v;
+            colj[t] = v;
+        }
+        __syncthreads();
+        for (int l = 1 + threadIdx.x; l <= w; l += blockDim.x) {
+            const double cl = colj[l];
+            if (cl == 0.0) continue;
+            for (int k0 = 1; k0 <= l; k0 += 16) {
+                double v[16];
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int k = k0 + u;
+                    if (k <= l) v[u] = B[(long long)(j + k) * (bw + 1) + (l - k)];
+                }
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int k = k0 + u;
+                    if (k <= l) B[(long long)(j + k) * (bw + 1) + (l - k)] = v[u] - cl * colj[k];
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && bad) atomicOr(flags, IETI_FLAG_NOT_SPD);
+}
+
+// (L L^T)^{-1} v in place on the slot's vector (global memory), one CTA.
+// Each step needs one column (forward) or one row (backward) of the factor:
+// thread t's entry for the step four ahead is loaded into a register ring,
+// so the L2 latency of the factor overlaps the preceding steps.
+__device__ void band_solve_loop(const double* B, int n, int bw, double* v) {
+    __shared__ double s;
+    const long long cs = bw + 1;
+    for (int j = 0; j < n; ++j) {
+        if (threadIdx.x == 0) {
+            s = v[j] / B[(long long)j * cs];
+            v[j] = s;
+        }
+        __syncthreads();
+        const int w = min(bw, n - 1 - j);
+        for (int t = 1 + threadIdx.x; t <= w; t += blockDim.x) v[j + t] -= B[(long long)j * cs + t] * s;
+        __syncthreads();
+    }
+    for (int j = n - 1; j >= 0; --j) {
+        if (threadIdx.x == 0) {
+            s = v[j] / B[(long long)j * cs];
+            v[j] = s;
+        }
+        __syncthreads();
+        const int w = min(bw, j);
+        for (int t = 1 + threadIdx.x; t <= w; t += blockDim.x) v[j - t] -= B[(long long)(j - t) * cs + t] * s;
+        __syncthreads();
+    }
+}
+
+__device__ void band_solve(const double* B, int n, int bw, double* v) {
+    if (bw >= (int)blockDim.x) {              // more band offsets than threads
+        band_solve_loop(B, n, bw, v);
+        return;
+    }
+    __shared__ double s;
+    const int t = 1 + threadIdx.x;            // this thread's offset in the band (t <= bw)
+    const bool act = t <= bw;
+    const long long cs = bw + 1;
+    auto fwd_entry = [&](int j) -> double {   // L(j + t, j)
+        return (act && j < n && t <= n - 1 - j) ? B[(long long)j * cs + t] : 0.0;
+    };
+    auto bwd_entry = [&](int j) -> double {   // L(j, j - t)
+        return (act && j >= 0 && t <= j) ? B[(long long)(j - t) * cs + t] : 0.0;
+    };
+    double ring[4];
+    for (int u = 0; u < 4; ++u) ring[u] = fwd_entry(u);
+    for (int j0 = 0; j0 < n; j0 += 4) {       // L y = v
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int j = j0 + u;
+            if (j >= n) break;
+            if (threadIdx.x == 0) {
+                s = v[j] / B[(long long)j * cs];
+                v[j] = s;
+            }
+            __syncthreads();
+            const double lj = ring[u];
+            ring[u] = fwd_entry(j + 4);
+            if (lj != 0.0) v[j + t] -= lj * s;
+            __syncthreads();
+        }
+    }
+    for (int u = 0; u < 4; ++u) ring[u] = bwd_entry(n - 1 - u);
+    for (int j0 = n - 1; j0 >= 0; j0 -= 4) {  // L^T x = y
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int j = j0 - u;
+            if (j < 0) break;
+            if (threadIdx.x == 0) {
+                s = v[j] / B[(long long)j * cs];
+                v[j] = s;
+            }
+            __syncthreads();
+            const double lj = ring[u];
+            ring[u] = bwd_entry(j - 4);
+            if (lj != 0.0) v[j - t] -= lj * s;
+            __syncthreads();
+        }
+    }
+}
+
+struct Red2 {
+    double v[32];
+};
+
+__device__ double cta_sum1(double x, Red2& sh) {
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh.v[w] = x;
+    __syncthreads();
+    double s = 0.0;
+    for (int i = 0; i < nw; ++i) s += sh.v[i];
+    __syncthreads();
+    return s;
+}
+
+// Neumann solve of one slot (patch): u = P z + Phi u_Pi with K z = P^T g
+// solved directly (same input and output conventions as the multigrid
+// Neumann mode of the local solver)
+__global__ void __launch_bounds__(1024) k_direct_neumann(SolveArgs a0) {
+    __shared__ SolveArgs sa;
+    __shared__ double coef[64];
+    __shared__ Red2 red;
+    const SlotDesc sd = a0.slots[blockIdx.x];
+    if (threadIdx.x == 0) {
+        sa = a0.batch ? a0.batch[sd.handle] : a0;
+        sa.slots = a0.slots;
+        sa.nslots = a0.nslots;
+    }
+    __syncthreads();
+    const SolveArgs& a = sa;
+    const PatchDesc& P = a.pd[sd.patch];
+    const LevelDesc& F = P.lev[P.L - 1];
+    const int n = F.n;
+    double* z = a.cg + sd.cg;
+    const double* g = a.in + P.toff;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int i0 = i % F.m[0], ir = i / F.m[0];
+        const int i1 = ir % F.m[1], i2 = ir / F.m[1];
+        z[i] = ieti_masked(P.dmask, F.m, i0, i1, i2) ? 0.0 : g[i];
+    }
+    __syncthreads();
+    // b = P^T g = g - C^T (Phi^T g)
+    {
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        for (int j = w; j < P.npi; j += nw) {
+            const int row = P.crow0 + j;
+            const double cj = a.rpi_loc[row];
+            for (int e = a.crow_ptr[row] + lane; e < a.crow_ptr[row + 1]; e += 32) z[a.c_idx[e]] -= a.c_w[e] * cj;
+        }
+    }
+    __syncthreads();
+    if (P.floating) {
+        // exact orthogonality to the constants (the kernel of K), then pin
+        double s = 0.0;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) s += z[i];
+        s = cta_sum1(s, red);
+        const double mean = s / n;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) z[i] -= mean;
+        __syncthreads();
+        if (threadIdx.x == 0 && P.pin >= 0) z[P.pin] = 0.0;
+        __syncthreads();
+    }
+    band_solve(a.band + P.bandoff, n, P.bw, z);
+    // u = z - Phi (C z - A u_Pi)
+    {
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        for (int j = w; j < P.npi; j += nw) {
+            const int row = P.crow0 + j;
+            double d = 0.0;
+            for (int e = a.crow_ptr[row] + lane; e < a.crow_ptr[row + 1]; e += 32) d += a.c_w[e] * z[a.c_idx[e]];
+            for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+            if (lane == 0) coef[j] = d - a.upi_loc[row];
+        }
+    }
+    __syncthreads();
+    double* out = a.out + P.toff;
+    const double* ph = a.phi + P.phioff;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double u = z[i];
+        for (int j = 0; j < P.npi; ++j) u -= coef[j] * ph[(long long)j * n + i];
+        out[i] = u;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_band_factor(const PatchDesc* pd, const int* plist, int npl, int max_n, int max_bw,
+                               const double* K64, double* band, int* flags, cudaStream_t st) {
+    if (npl == 0) return cudaSuccess;
+    k_band_assemble<<<dim3((max_n + 255) / 256, npl), 256, 0, st>>>(pd, plist, K64, band);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const size_t sm = sizeof(double) * (size_t)(max_bw + 1);
+    if (sm > 48 * 1024) {
+        e = cudaFuncSetAttribute(k_band_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+    }
+    k_band_cholesky<<<npl, 256, sm, st>>>(pd, plist, band, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_direct_neumann(const SolveArgs& a, int max_bw, cudaStream_t st) {
+    if (a.nslots == 0) return cudaSuccess;
+    // one thread per band offset (the solve's inner loops are unit-stride per step)
+    const int threads = std::min(1024, std::max(64, ((max_bw + 31) / 32) * 32));
+    k_direct_neumann<<<a.nslots, threads, 0, st>>>(a);
+    return cudaGetLastError();
+}

@@ -130,6 +130,8 @@ struct ietidp_handle {
     double* phi = nullptr;
     double* szW = nullptr;        // SZ basis: Khat^{-1} C^T (layout of phi)
     double* szHinv = nullptr;     // SZ basis: Hhat^{-1} per patch
+    double* band = nullptr;       // D-MG: banded Cholesky factors of the fine stiffness
+    int max_bw = 0;               // D-MG: largest half band width of the patches
     double* Linv = nullptr;
     std::vector<double> spp_host;
     double *rloc = nullptr, *upi = nullptr, *uloc = nullptr;

@@ -86,6 +86,7 @@ struct MGroup {
     size_t smem = 0;       // shared memory of the handles' own plan (max)
     size_t smem_min = 0;   // shared memory the kernel cannot do without (max)
     size_t tab_min = 0;    // color tables alone (minimum of the global-vector variant)
+    int max_bw = 0;        // direct Neumann solves: largest half band width
     TuneCfg cfg{512, 0, 1, 0.f, 0};
 };
 
@@ -174,6 +175,7 @@ int ensure_side(ieti_engine* E, size_t n) {
 cudaError_t launch_cfg(const SolveArgs& a, const MGroup& g, const TuneCfg& c, cudaStream_t st) {
     SolveArgs b = a;
     b.smem_bytes = c.smem;
+    if (g.kind == 3) return launch_direct_neumann(b, g.max_bw, st);
     if (g.kind == 2) return launch_solve(b, c.threads, st);
     return launch_solve_variant(b, g.dim, g.p0, g.p1, g.p2, c.threads, st, g.kind == 1 || c.xg);
 }
@@ -211,7 +213,7 @@ std::vector<TuneCfg> candidates(const MGroup& g) {
 // real launch) and keep the fastest; cached per launch shape
 int tune(ieti_engine* E, MGroup& g, const std::vector<ietidp_handle*>& hs, long long* nlaunch) {
     g.cfg = TuneCfg{512, g.smem, 1, 0.f, 0};
-    if (g.kind == 2 || !autotune_enabled()) return IETIDP_OK;
+    if (g.kind >= 2 || !autotune_enabled()) return IETIDP_OK;
     TuneKey key{g.dim, g.p0, g.p1, g.p2, g.kind, g.mixed,
                 (int)((g.s.size() + sm_count() - 1) / sm_count()),
                 *std::max_element(g.cost.begin(), g.cost.end())};
@@ -293,9 +295,12 @@ int merged_launch(ieti_engine* E, Staging& S, std::vector<std::pair<ietidp_handl
     for (size_t i = 0; i < items.size(); ++i) {
         ietidp_handle* h = items[i].first;
         const int mixed = h->opt.precision == IETIDP_PREC_MIXED;
+        const bool direct = items[i].second.mode == MODE_NEUMANN_DIRECT;
         for (const SlotGroup& sg : h->gpatch) {
-            const int kind = sg.generic ? 2 : (sg.xg ? 1 : 0);
-            MGroup& m = by[std::make_tuple(sg.dim, sg.p0, sg.p1, sg.p2, kind, mixed)];
+            // kind 3: direct Neumann solves (one kernel for every degree)
+            const int kind = direct ? 3 : (sg.generic ? 2 : (sg.xg ? 1 : 0));
+            MGroup& m = direct ? by[std::make_tuple(0, 0, 0, 0, 3, mixed)]
+                               : by[std::make_tuple(sg.dim, sg.p0, sg.p1, sg.p2, kind, mixed)];
             m.dim = sg.dim;
             m.p0 = sg.p0;
             m.p1 = sg.p1;
@@ -303,6 +308,7 @@ int merged_launch(ieti_engine* E, Staging& S, std::vector<std::pair<ietidp_handl
             m.kind = kind;
             m.mixed = mixed;
             m.smem = std::max(m.smem, sg.smem);
+            m.max_bw = std::max(m.max_bw, h->max_bw);
             for (SlotDesc sd : sg.hs) {
                 sd.handle = (int)i;
                 const PatchDesc& P = h->pd[sd.patch];

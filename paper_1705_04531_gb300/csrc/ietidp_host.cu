@@ -394,7 +394,8 @@ static int launch_group(ietidp_handle* h, SolveArgs a, const SlotGroup& g, cudaS
     a.its = h->its;
     a.smem_bytes = g.smem;
     cudaError_t e;
-    if (!g.generic) e = launch_solve_variant(a, g.dim, g.p0, g.p1, g.p2, 512, st, g.xg);
+    if (a.mode == MODE_NEUMANN_DIRECT) e = launch_direct_neumann(a, h->max_bw, st);
+    else if (!g.generic) e = launch_solve_variant(a, g.dim, g.p0, g.p1, g.p2, 512, st, g.xg);
     else e = launch_solve(a, 512, st);
     h->launches += 1;
     g_kernel_launches += 1;
@@ -441,6 +442,8 @@ SolveArgs ieti_solve_args(const ietidp_handle* h, int mode, const double* in, do
     a.batch = nullptr;
     a.szW = h->szW;
     a.szHinv = h->szHinv;
+    a.band = h->band;
+    if (mode == MODE_NEUMANN && h->opt.method == IETIDP_METHOD_DMG) a.mode = MODE_NEUMANN_DIRECT;
     return a;
 }
 
@@ -521,7 +524,8 @@ extern "C" int ietidp_setup(const iga_problem* P, const ietidp_options* opt_in, 
         opt.maxit_inner < 1 || opt.maxit_outer < 0 || !(opt.tol_outer > 0) || !(opt.tol_inner > 0) ||
         !(opt.tol_basis > 0) || opt.alpha_reg < 0)
         return fail(IETIDP_E_INVALID_ARG, "bad options");
-    if ((opt.method != IETIDP_METHOD_DUAL && opt.method != IETIDP_METHOD_SADDLE) || opt.saddle_vcycles < 1 ||
+    if ((opt.method != IETIDP_METHOD_DUAL && opt.method != IETIDP_METHOD_SADDLE && opt.method != IETIDP_METHOD_DMG) ||
+        opt.saddle_vcycles < 1 ||
         !(opt.saddle_theta > 0 && opt.saddle_theta < 1) ||
         (opt.basis_method != IETIDP_BASIS_SZ && opt.basis_method != IETIDP_BASIS_NULLSPACE))
         return fail(IETIDP_E_INVALID_ARG, "bad method options");
@@ -702,7 +706,7 @@ extern "C" int ietidp_setup(const iga_problem* P, const ietidp_options* opt_in, 
     }
     // ---- levels and descriptors ----------------------------------------------
     h->pd.resize(N);
-    long long koff = 0, toff_tab = 0, itoff = 0, a0off = 0, phioff = 0, szhoff = 0;
+    long long koff = 0, toff_tab = 0, itoff = 0, a0off = 0, phioff = 0, szhoff = 0, bandoff = 0;
     int max_n0 = 1, max_S = 1, max_rows_lev = 1, max_L = 1;
     std::vector<TableJob> tjobs, mjobs;
     long long cg_need = 0, lv_need = 0;
@@ -784,6 +788,15 @@ extern "C" int ietidp_setup(const iga_problem* P, const ietidp_options* opt_in, 
         phioff += (long long)q.n * q.npi;
         q.szhoff = szhoff;
         szhoff += (long long)q.npi * q.npi;
+        q.bw = q.p[0] + q.lev[q.L - 1].m[0] * (q.p[1] + q.lev[q.L - 1].m[1] * q.p[2]);
+        q.pin = -1;
+        q.bandoff = 0;
+        if (opt.method == IETIDP_METHOD_DMG) {
+            const int* mm = q.lev[q.L - 1].m;
+            if (q.floating) q.pin = mm[0] / 2 + mm[0] * (mm[1] / 2 + mm[1] * (mm[2] / 2));
+            q.bandoff = bandoff;
+            bandoff += (long long)q.n * (q.bw + 1);
+        }
         cg_need = std::max(cg_need, (long long)q.n);
         lv_need = std::max(lv_need, (long long)q.nlvec);
         if (toff_tab > (1LL << 31) - 1 || itoff > (1LL << 31) - 1) return bail(fail(IETIDP_E_INVALID_ARG, "tables too large"));
@@ -814,6 +827,7 @@ extern "C" int ietidp_setup(const iga_problem* P, const ietidp_options* opt_in, 
     CKH(h->mem.upload(&d_tang, crow_tang_v, st));
     CKH(h->mem.alloc(&h->c_w, (long long)c_idx.size()));
     CKH(h->mem.alloc(&h->phi, phioff));
+    if (opt.method == IETIDP_METHOD_DMG) CKH(h->mem.alloc(&h->band, bandoff));
     const bool sz = opt.basis_method == IETIDP_BASIS_SZ;
     if (sz) {
         CKH(h->mem.alloc(&h->szW, phioff));
@@ -973,6 +987,33 @@ extern "C" int ietidp_setup(const iga_problem* P, const ietidp_options* opt_in, 
             }
             CUH(cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming));
         }
+    }
+    // ---- D-MG: banded Cholesky factors of the fine stiffness ---------------
+    if (opt.method == IETIDP_METHOD_DMG) {
+        std::vector<int> plist(N);
+        int max_n = 0;
+        for (int k = 0; k < N; ++k) {
+            plist[k] = k;
+            max_n = std::max(max_n, h->pd[k].n);
+            h->max_bw = std::max(h->max_bw, h->pd[k].bw);
+            // the band factorization costs n bw^2 per patch: kept for patches
+            // where that stays moderate (2D patches; large 3D patches are
+            // what the paper's direct variants could not hold either)
+            const double cost = (double)h->pd[k].n * h->pd[k].bw * h->pd[k].bw;
+            if (cost > 2e10)
+                return bail(fail(IETIDP_E_INVALID_ARG, "D-MG: banded factorization of patch " + std::to_string(k) +
+                                                           " too large (n = " + std::to_string(h->pd[k].n) +
+                                                           ", band " + std::to_string(h->pd[k].bw) + ")"));
+        }
+        int* d_plist;
+        CKH(h->mem.upload(&d_plist, plist, st));
+        CUH(cudaMemsetAsync(h->band, 0, sizeof(double) * bandoff, st));
+        CUH(cudaMemsetAsync(h->flags, 0, sizeof(int), st));
+        CUH(launch_band_factor(h->d_pd, d_plist, N, max_n, h->max_bw, h->K64, h->band, h->flags, st));
+        int fl = 0;
+        CUH(cudaMemcpyAsync(&fl, h->flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CUH(cudaStreamSynchronize(st));
+        if (fl & IETI_FLAG_NOT_SPD) return bail(fail(IETIDP_E_BREAKDOWN, "banded Cholesky: stiffness not SPD"));
     }
     // ---- primal basis (Eq. 6) ---------------------------------------------
     if (nslot_basis > 0) {

@@ -58,6 +58,10 @@ cudaError_t launch_cweights(const PatchDesc* pd, int nrows, const int* crow_ptr,
 
 cudaError_t launch_to_f32(const double* src, float* dst, long long n, cudaStream_t st);
 
+// D-MG: band of the fine K (Dirichlet and pinned dofs as identity rows) and its
+// Cholesky factor, one CTA per listed patch (direct_kernels.cu)
+cudaError_t launch_band_factor(const PatchDesc* pd, const int* plist, int npl, int max_n, int max_bw,
+                               const double* K64, double* band, int* flags, cudaStream_t st);
 // SZ basis: Hhat^{-1} = (0.99 C W)^{-1} per patch (W = Khat^{-1} C^T, layout of phi)
 cudaError_t launch_sz_hinv(const PatchDesc* pd, int npatch, const int* crow_ptr, const int* c_idx,
                            const double* c_w, const double* szW, double* szHinv, int* flags, cudaStream_t st);
@@ -93,7 +97,8 @@ enum SlotMode {
     MODE_POWER = 4,
     MODE_KHAT = 5,
     MODE_SZW = 6,
-    MODE_BASIS_SZ = 7
+    MODE_BASIS_SZ = 7,
+    MODE_NEUMANN_DIRECT = 8   // D-MG: Neumann solve by the banded Cholesky factor
 };
 
 struct SolveArgs {
@@ -132,6 +137,7 @@ struct SolveArgs {
     double* omega;             // per patch BPCG scaling (written by the power mode, read by K-hat)
     double* szW;               // SZ basis: W = Khat^{-1} C^T pool (layout of phi)
     const double* szHinv;      // SZ basis: Hhat^{-1} pool (PatchDesc::szhoff)
+    const double* band;        // D-MG: banded Cholesky factors (PatchDesc::bandoff)
     long long* vstats;         // [0] V-cycles, [1] V-cycle fine dofs (atomically added)
     size_t smem_bytes;         // dynamic shared memory of the launch (specialised kernels)
     int* dbg;                  // self-check record (debug builds only)
@@ -144,6 +150,9 @@ struct SolveArgs {
 
 // generic kernel (degrees known at run time only)
 cudaError_t launch_solve(const SolveArgs& a, int threads, cudaStream_t st);
+// D-MG: Neumann solves of the slots by the banded Cholesky factors (same
+// input / output conventions as MODE_NEUMANN)
+cudaError_t launch_direct_neumann(const SolveArgs& a, int max_bw, cudaStream_t st);
 // kernel specialised for (dim, p0, p1, p2); cudaErrorNotSupported if none exists
 bool solve_variant_exists(int dim, int p0, int p1, int p2, int mixed);
 // xg: V-cycle vectors in global memory (patches whose vectors exceed the

@@ -32,7 +32,7 @@ IGA_GEO_BOX, IGA_GEO_ANNULUS = 0, 1
 RHS = {"none": 0, "sin2d": 1, "sin3d": 2, "annulus": 3, "modes": 4, "quad": 5}
 PRIMAL = {"vertex": 1, "edge": 2, "face": 4}
 PREC_FP64, PREC_MIXED = 0, 1
-METHOD = {"dual": 0, "saddle": 1}
+METHOD = {"dual": 0, "saddle": 1, "dmg": 2}
 BASIS = {"sz": 0, "nullspace": 1}
 
 

@@ -1,0 +1,74 @@
+"""D-MG on the GPU (method IETIDP_METHOD_DMG, Sec. 3.3): direct local Neumann
+solves by banded Cholesky (pinned dof on floating patches), multigrid
+Dirichlet problems, through the C ABI against the CPU oracle's D-MG mode.
+
+Bars: relative solution error <= 1e-8 against the conforming direct solve
+(FP64 and mixed V-cycles in the preconditioner); outer iterations within +-1
+of the oracle's D-MG; batched = single; the factorization guard rejects a
+band too large to factor."""
+import numpy as np
+import pytest
+
+from oracle import ietidp as O
+from oracle.domain import Multipatch
+from paper_1705_04531_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1705_04531_gb300 import build
+    build.build()
+    from paper_1705_04531_gb300 import ietidp
+    return ietidp
+
+
+def relerr(got, ref):
+    return np.sqrt(sum(np.sum((a - b) ** 2) for a, b in zip(got, ref)) / sum(np.sum(b ** 2) for b in ref))
+
+
+DOMS = {
+    "square_rq": lambda: W.random_quad_rhs(W.square_2x2(16, 2), seed=41),
+    "annulus3x3": lambda: W.annulus_6x6(8, 3, grid=(3, 3)),
+    "uneven3x3": lambda: W.random_quad_rhs(W.uneven_8x8(0, grid=(3, 3), nelems=(8, 16, 32)), seed=42),
+    "modes4x4": lambda: W.uniform_grid(2, (4, 4), 3, 16, W.UNIT,
+                                       W.sine_modes_rhs(np.random.default_rng(43)), ("vertex", "edge")),
+    "cube_rq": lambda: W.random_quad_rhs(W.cube_2x2x2(8, 2), seed=44),
+}
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("name", list(DOMS))
+def test_dmg_matches_direct_and_oracle(api, name, prec):
+    dom = DOMS[name]()
+    mp = Multipatch(dom)
+    ref = mp.to_patches(mp.solve_global())
+    sol = api.Solver(api.Problem(dom), precision=prec, method="dmg")
+    u, st = sol.solve()
+    err = relerr(sol.split(u), ref)
+    assert st["converged"] and err <= 1e-8, (err, st)
+    orc = O.IETIDP(dom, O.Options(mode="dmg"))
+    orc.solve()
+    assert abs(st["outer_it"] - orc.stats.outer_it) <= 1, (st["outer_it"], orc.stats.outer_it)
+
+
+def test_dmg_batch_equals_single(api):
+    doms = [DOMS[n]() for n in ("square_rq", "annulus3x3", "uneven3x3")]
+    sols = [api.Solver(api.Problem(d), precision="mixed", method="dmg") for d in doms]
+    singles = [s.solve()[0].clone() for s in sols]
+    us, sts = api.Solver.solve_batch(sols)
+    for s, a, b, st in zip(sols, singles, us, sts):
+        assert st["converged"]
+        assert relerr(s.split(b), s.split(a)) <= 1e-10
+
+
+def test_dmg_rejects_oversized_band(api):
+    # 2x2x2 cube, p=2, 32^3 elements per patch: band 2382, n 39304 -> n bw^2 ~ 2.2e11
+    prob = api.Problem(W.cube_2x2x2(32, 2))
+    with pytest.raises(api.IetidpError) as e:
+        api.Solver(prob, method="dmg")
+    assert api.ERRORS[e.value.code] == "INVALID_ARG"

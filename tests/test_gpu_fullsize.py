@@ -81,11 +81,11 @@ def annulus_ref():
     return dom, mp.to_patches(mp.solve_global())
 
 
-@pytest.mark.parametrize("method", ["dual", "saddle"])
+@pytest.mark.parametrize("method", ["dual", "saddle", "dmg"])
 def test_annulus_batch_of_8_as_benchmarked(api, annulus_ref, method):
     """The benchmark's step: 8 copies of the annulus in one lockstep batch
     (mixed; the tuned 256-thread, 2-CTA-per-SM launches), every copy against
-    the direct solve; MG-MG and MG-MG-S."""
+    the direct solve; MG-MG, MG-MG-S and D-MG."""
     dom, ref = annulus_ref
     probs = [api.Problem(dom) for _ in range(8)]
     sols = [api.Solver(p, precision="mixed", method=method) for p in probs]
