@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--concurrency", type=int, default=8, help="serve: worker streams")
     ap.add_argument("--budget-gb", type=float, default=64.0, help="serve: device memory budget")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--method", default="dual", choices=["dual", "saddle", "dmg"],
+                    help="serve / profile: outer method (MG-MG, MG-MG-S, D-MG)")
     ap.add_argument("--batch", type=int, default=8,
                     help="independent copies of the workload solved in lockstep per step")
     return ap.parse_args()
@@ -354,7 +356,7 @@ def run_serve(args):
     from paper_1705_04531_gb300 import ietidp as api
     stream = W.serving_stream(nreq=args.nreq, rate=args.rate, seed=0)
     srv = api.Server(int(args.budget_gb * (1 << 30)), max_concurrent=args.concurrency,
-                     precision=args.precision)
+                     precision=args.precision, method=args.method)
     # warm-up: one small request (module load, kernel attributes)
     srv.wait(srv.submit(W.serving_stream(nreq=1, rate=1.0, seed=99, ms=(2,), ns=(16,))[0].domain))
     torch.cuda.synchronize()
@@ -380,7 +382,8 @@ def run_serve(args):
             "run_p50_ms": 1e3 * float(np.percentile(runs, 50)),
             "config": {"workload": "serving stream (m in {2,4,6,8}, p in {2,3}, n in {16,32,64,128})",
                        "requests": len(stream), "rate_per_s": args.rate, "concurrency": args.concurrency,
-                       "budget_gb": args.budget_gb, "precision": args.precision, "torn_dofs_total": dofs},
+                       "budget_gb": args.budget_gb, "precision": args.precision, "method": args.method,
+                       "torn_dofs_total": dofs},
             "outer_it_mean": float(np.mean(its)), "wall_s": t1 - t0}
     print(json.dumps(line), flush=True)
 

@@ -80,11 +80,18 @@ long long estimate_bytes(const Request& r, const ietidp_options& o) {
         per_val += 8 + (mixed ? 4 : 0);              // K + alpha M^ copies (floating patches; bound)
         b += n * S * per_val * lev;
         b += n * S * 8;                              // the problem's fine stiffness
-        b += n * 26 * 8;                             // primal basis (<= 26 constraints per patch)
-        b += n * 5 * 8 * 4;                          // CG vectors of patch and basis slots
+        b += n * 26 * 8 * 2;                         // primal basis and SZ W (<= 26 constraints per patch)
+        b += n * 8 * 8 * 4;                          // CG vectors of patch and basis slots
+        if (o.method == IETIDP_METHOD_DMG) {         // banded Cholesky factor
+            const int d = r.dim;
+            const long long m0 = p.nelem[0] + p.degree[0], m1 = d > 1 ? p.nelem[1] + p.degree[1] : 1;
+            const long long bw = p.degree[0] + m0 * ((d > 1 ? p.degree[1] : 0) + m1 * (d > 2 ? p.degree[2] : 0));
+            b += n * (bw + 1) * 8;
+        }
         b += n * 4 * 8 * lev;                        // level vectors
     }
     b += ntorn * 12 * 8;                             // torn buffers
+    if (o.method == IETIDP_METHOD_SADDLE) b += ntorn * 11 * 8;   // BPCG vectors
     b += qp * 7 * 8;                                 // assembly scratch (geometry factors, loads)
     b += 64LL << 20;                                 // tables, coarse matrices, dual vectors, slack
     return b;
