@@ -108,3 +108,32 @@ def test_autotune_records_and_can_be_disabled(api):
     us1, st1 = api.Solver.solve_batch(sols)
     for a, b in zip(us0, us1):
         assert relerr([a.cpu().numpy()], [b.cpu().numpy()]) <= 1e-10
+
+
+@pytest.mark.parametrize("method", ["dual", "saddle", "dmg"])
+def test_zero_load_gives_zero_solution(api, method):
+    """Degenerate input: f = 0 gives u = 0 at once (zero dual right-hand side,
+    or zero first BPCG inner product), in every method."""
+    dom = W.annulus_6x6(8, 3, grid=(3, 3))
+    sol = api.Solver(api.Problem(dom), precision="mixed", method=method)
+    f = torch.zeros(sol.n_torn, dtype=torch.float64, device="cuda")
+    u, st = sol.solve(f)
+    assert st["converged"]
+    assert float(u.abs().max()) == 0.0
+    assert st["outer_it"] == 0
+
+
+def test_graph_replay_equals_eager(api):
+    """The CUDA-graph replay of the per-iteration launches gives the same bits
+    as eager launches."""
+    dom = W.annulus_6x6(8, 3, grid=(3, 3))
+    sol = api.Solver(api.Problem(dom), precision="mixed")
+    u1, st1 = sol.solve()
+    u1 = u1.clone()
+    os.environ["IETIDP_GRAPHS"] = "0"
+    try:
+        u0, st0 = sol.solve()
+    finally:
+        del os.environ["IETIDP_GRAPHS"]
+    assert torch.equal(u0, u1)
+    assert st0["outer_it"] == st1["outer_it"]
