@@ -9,7 +9,8 @@
 // constants -- P^T g is -- the pinned system gives one solution of K z = P^T g,
 // and the energy projection P removes the constant in which the solutions
 // differ (Sec. 3.2: w = P z).  The band is stored by columns, lower part:
-// band[bandoff + j (bw+1) + (i - j)] = L(i, j) for j <= i <= j + bw.
+// band[bandoff + j (bw+1) + (i - j)] = L(i, j) for j < i <= j + bw, and the
+// reciprocal 1 / L(j, j) in place of the diagonal (the solves multiply).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -79,7 +80,7 @@ __global__ void k_band_cholesky(const PatchDesc* pd, const int* plist, double* b
             const double a = cj[0];
             if (!(a > 0.0)) bad = 1;
             const double d = a > 0.0 ? sqrt(a) : 1.0;
-            cj[0] = d;
+            cj[0] = 1.0 / d;
             colj[0] = d;
         }
         __syncthreads();
@@ -113,16 +114,14 @@ __global__ void k_band_cholesky(const PatchDesc* pd, const int* plist, double* b
     if (threadIdx.x == 0 && bad) atomicOr(flags, IETI_FLAG_NOT_SPD);
 }
 
-// (L L^T)^{-1} v in place on the slot's vector (global memory), one CTA.
-// Each step needs one column (forward) or one row (backward) of the factor:
-// thread t's entry for the step four ahead is loaded into a register ring,
-// so the L2 latency of the factor overlaps the preceding steps.
+// (L L^T)^{-1} v in place, one CTA (v in shared or global memory).  Each
+// step needs one column (forward) or one row (backward) of the factor.
 __device__ void band_solve_loop(const double* B, int n, int bw, double* v) {
     __shared__ double s;
     const long long cs = bw + 1;
     for (int j = 0; j < n; ++j) {
         if (threadIdx.x == 0) {
-            s = v[j] / B[(long long)j * cs];
+            s = v[j] * B[(long long)j * cs];
             v[j] = s;
         }
         __syncthreads();
@@ -132,7 +131,7 @@ __device__ void band_solve_loop(const double* B, int n, int bw, double* v) {
     }
     for (int j = n - 1; j >= 0; --j) {
         if (threadIdx.x == 0) {
-            s = v[j] / B[(long long)j * cs];
+            s = v[j] * B[(long long)j * cs];
             v[j] = s;
         }
         __syncthreads();
@@ -142,14 +141,22 @@ __device__ void band_solve_loop(const double* B, int n, int bw, double* v) {
     }
 }
 
+// Thread t-1 owns band offset t (t <= bw < blockDim).  One barrier per step:
+// thread 0 (offset 1) makes the last update of the next pivot's entry, so it
+// also finishes that pivot (multiplies by the stored reciprocal diagonal)
+// and publishes it in the other half of a double buffer.  The factor entries
+// of the step four ahead (and, for thread 0, the reciprocal diagonals) are
+// loaded into register rings, so their L2 latency overlaps the steps before.
 __device__ void band_solve(const double* B, int n, int bw, double* v) {
+    if (n <= 0) return;
     if (bw >= (int)blockDim.x) {              // more band offsets than threads
         band_solve_loop(B, n, bw, v);
         return;
     }
-    __shared__ double s;
+    __shared__ double piv[2];
     const int t = 1 + threadIdx.x;            // this thread's offset in the band (t <= bw)
     const bool act = t <= bw;
+    const bool lead = threadIdx.x == 0;
     const long long cs = bw + 1;
     auto fwd_entry = [&](int j) -> double {   // L(j + t, j)
         return (act && j < n && t <= n - 1 - j) ? B[(long long)j * cs + t] : 0.0;
@@ -157,38 +164,67 @@ __device__ void band_solve(const double* B, int n, int bw, double* v) {
     auto bwd_entry = [&](int j) -> double {   // L(j, j - t)
         return (act && j >= 0 && t <= j) ? B[(long long)(j - t) * cs + t] : 0.0;
     };
-    double ring[4];
-    for (int u = 0; u < 4; ++u) ring[u] = fwd_entry(u);
+    auto rdiag = [&](int j) -> double {       // 1 / L(j, j), thread 0 only
+        return (lead && j >= 0 && j < n) ? B[(long long)j * cs] : 0.0;
+    };
+    double ring[4], dring[4];
+    for (int u = 0; u < 4; ++u) {
+        ring[u] = fwd_entry(u);
+        dring[u] = rdiag(u + 1);
+    }
+    if (lead) {
+        const double s0 = v[0] * B[0];
+        v[0] = s0;
+        piv[0] = s0;
+    }
+    __syncthreads();
     for (int j0 = 0; j0 < n; j0 += 4) {       // L y = v
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int j = j0 + u;
             if (j >= n) break;
-            if (threadIdx.x == 0) {
-                s = v[j] / B[(long long)j * cs];
-                v[j] = s;
-            }
-            __syncthreads();
+            const double s = piv[j & 1];
             const double lj = ring[u];
             ring[u] = fwd_entry(j + 4);
             if (lj != 0.0) v[j + t] -= lj * s;
+            if (lead) {
+                if (j + 1 < n) {
+                    const double sn = v[j + 1] * dring[u];
+                    v[j + 1] = sn;
+                    piv[(j + 1) & 1] = sn;
+                }
+                dring[u] = rdiag(j + 5);
+            }
             __syncthreads();
         }
     }
-    for (int u = 0; u < 4; ++u) ring[u] = bwd_entry(n - 1 - u);
+    for (int u = 0; u < 4; ++u) {
+        ring[u] = bwd_entry(n - 1 - u);
+        dring[u] = rdiag(n - 2 - u);
+    }
+    if (lead) {
+        const double s0 = v[n - 1] * B[(long long)(n - 1) * cs];
+        v[n - 1] = s0;
+        piv[(n - 1) & 1] = s0;
+    }
+    __syncthreads();
     for (int j0 = n - 1; j0 >= 0; j0 -= 4) {  // L^T x = y
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int j = j0 - u;
             if (j < 0) break;
-            if (threadIdx.x == 0) {
-                s = v[j] / B[(long long)j * cs];
-                v[j] = s;
-            }
-            __syncthreads();
+            const double s = piv[j & 1];
             const double lj = ring[u];
             ring[u] = bwd_entry(j - 4);
             if (lj != 0.0) v[j - t] -= lj * s;
+            if (lead) {
+                if (j >= 1) {
+                    const double sn = v[j - 1] * dring[u];
+                    v[j - 1] = sn;
+                    piv[(j - 1) & 1] = sn;
+                }
+                dring[u] = rdiag(j - 5);
+            }
             __syncthreads();
         }
     }
@@ -213,7 +249,8 @@ __device__ double cta_sum1(double x, Red2& sh) {
 // Neumann solve of one slot (patch): u = P z + Phi u_Pi with K z = P^T g
 // solved directly (same input and output conventions as the multigrid
 // Neumann mode of the local solver)
-__global__ void __launch_bounds__(1024) k_direct_neumann(SolveArgs a0) {
+__global__ void __launch_bounds__(512) k_direct_neumann(SolveArgs a0) {
+    extern __shared__ double zsh[];
     __shared__ SolveArgs sa;
     __shared__ double coef[64];
     __shared__ Red2 red;
@@ -228,7 +265,9 @@ __global__ void __launch_bounds__(1024) k_direct_neumann(SolveArgs a0) {
     const PatchDesc& P = a.pd[sd.patch];
     const LevelDesc& F = P.lev[P.L - 1];
     const int n = F.n;
-    double* z = a.cg + sd.cg;
+    // the substitution's vector in shared memory when it fits the launch's
+    // dynamic budget (every step reads and updates it), else in global memory
+    double* z = (size_t)n * sizeof(double) <= a0.smem_bytes ? zsh : a.cg + sd.cg;
     const double* g = a.in + P.toff;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const int i0 = i % F.m[0], ir = i / F.m[0];
@@ -299,7 +338,12 @@ cudaError_t launch_band_factor(const PatchDesc* pd, const int* plist, int npl, i
 cudaError_t launch_direct_neumann(const SolveArgs& a, int max_bw, cudaStream_t st) {
     if (a.nslots == 0) return cudaSuccess;
     // one thread per band offset (the solve's inner loops are unit-stride per step)
-    const int threads = std::min(1024, std::max(64, ((max_bw + 31) / 32) * 32));
-    k_direct_neumann<<<a.nslots, threads, 0, st>>>(a);
+    const int threads = std::min(512, std::max(64, ((max_bw + 32) / 32) * 32));
+    cudaError_t e = cudaFuncSetAttribute(k_direct_neumann, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kDirectSmemCap);
+    if (e != cudaSuccess) return e;
+    SolveArgs b = a;
+    b.smem_bytes = std::min(a.smem_bytes, kDirectSmemCap);
+    k_direct_neumann<<<a.nslots, threads, b.smem_bytes, st>>>(b);
     return cudaGetLastError();
 }

@@ -132,6 +132,7 @@ struct ietidp_handle {
     double* szHinv = nullptr;     // SZ basis: Hhat^{-1} per patch
     double* band = nullptr;       // D-MG: banded Cholesky factors of the fine stiffness
     int max_bw = 0;               // D-MG: largest half band width of the patches
+    size_t direct_smem = 0;       // D-MG: shared memory of the substitution vector (largest patch that fits)
     double* Linv = nullptr;
     std::vector<double> spp_host;
     double *rloc = nullptr, *upi = nullptr, *uloc = nullptr;

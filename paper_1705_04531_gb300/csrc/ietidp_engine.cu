@@ -307,7 +307,7 @@ int merged_launch(ieti_engine* E, Staging& S, std::vector<std::pair<ietidp_handl
             m.p2 = sg.p2;
             m.kind = kind;
             m.mixed = mixed;
-            m.smem = std::max(m.smem, sg.smem);
+            m.smem = std::max(m.smem, direct ? h->direct_smem : sg.smem);
             m.max_bw = std::max(m.max_bw, h->max_bw);
             for (SlotDesc sd : sg.hs) {
                 sd.handle = (int)i;

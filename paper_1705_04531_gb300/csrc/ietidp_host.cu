@@ -394,8 +394,10 @@ static int launch_group(ietidp_handle* h, SolveArgs a, const SlotGroup& g, cudaS
     a.its = h->its;
     a.smem_bytes = g.smem;
     cudaError_t e;
-    if (a.mode == MODE_NEUMANN_DIRECT) e = launch_direct_neumann(a, h->max_bw, st);
-    else if (!g.generic) e = launch_solve_variant(a, g.dim, g.p0, g.p1, g.p2, 512, st, g.xg);
+    if (a.mode == MODE_NEUMANN_DIRECT) {
+        a.smem_bytes = h->direct_smem;
+        e = launch_direct_neumann(a, h->max_bw, st);
+    } else if (!g.generic) e = launch_solve_variant(a, g.dim, g.p0, g.p1, g.p2, 512, st, g.xg);
     else e = launch_solve(a, 512, st);
     h->launches += 1;
     g_kernel_launches += 1;
@@ -996,6 +998,8 @@ extern "C" int ietidp_setup(const iga_problem* P, const ietidp_options* opt_in, 
             plist[k] = k;
             max_n = std::max(max_n, h->pd[k].n);
             h->max_bw = std::max(h->max_bw, h->pd[k].bw);
+            const size_t zb = sizeof(double) * (size_t)h->pd[k].n;
+            if (zb <= kDirectSmemCap) h->direct_smem = std::max(h->direct_smem, zb);
             // the band factorization costs n bw^2 per patch: kept for patches
             // where that stays moderate (2D patches; large 3D patches are
             // what the paper's direct variants could not hold either)

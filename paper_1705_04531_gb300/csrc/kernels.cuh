@@ -151,7 +151,9 @@ struct SolveArgs {
 // generic kernel (degrees known at run time only)
 cudaError_t launch_solve(const SolveArgs& a, int threads, cudaStream_t st);
 // D-MG: Neumann solves of the slots by the banded Cholesky factors (same
-// input / output conventions as MODE_NEUMANN)
+// input / output conventions as MODE_NEUMANN); a.smem_bytes: dynamic shared
+// memory for the substitution vector (slots whose n doubles fit use it)
+constexpr size_t kDirectSmemCap = 160 * 1024;
 cudaError_t launch_direct_neumann(const SolveArgs& a, int max_bw, cudaStream_t st);
 // kernel specialised for (dim, p0, p1, p2); cudaErrorNotSupported if none exists
 bool solve_variant_exists(int dim, int p0, int p1, int p2, int mixed);
