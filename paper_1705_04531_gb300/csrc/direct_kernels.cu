@@ -60,52 +60,86 @@ __global__ void k_band_assemble(const PatchDesc* pd, const int* plist, const dou
     }
 }
 
-// right-looking band Cholesky, one CTA per patch: column j is scaled and
-// kept in shared memory, then every row l of the trailing window subtracts
-// L(j+l, j) L(j+k, j) from A(j+l, j+k), k <= l; a thread owns a row l and
-// reads/writes 16 of its entries per batch (loads issued together), lanes of
-// a warp own consecutive rows (coalesced per k)
-__global__ void k_band_cholesky(const PatchDesc* pd, const int* plist, double* band, int* flags) {
-    extern __shared__ double colj[];
+// right-looking band Cholesky by panels of kPanel columns, one CTA per patch.
+// A panel (its columns' band entries, already updated by every earlier panel)
+// is factored in shared memory, written back (reciprocal diagonal), and then
+// applied once to the trailing window as a rank-kPanel update: every entry
+// A(r, c') with c' past the panel and r <= last panel column + bw loses
+// sum_c L(r, c) L(c', c) over the panel columns c.  One warp per trailing
+// column, lanes over its rows (coalesced), four rows per lane in flight.
+constexpr int kPanel = 8;
+
+__global__ void __launch_bounds__(256) k_band_cholesky(const PatchDesc* pd, const int* plist, double* band,
+                                                       int* flags) {
+    extern __shared__ double pan[];           // [kPanel][bw + 1]
     __shared__ int bad;
     const PatchDesc& P = pd[plist[blockIdx.x]];
     const int n = P.n, bw = P.bw;
+    const long long cs = bw + 1;
     double* B = band + P.bandoff;
     if (threadIdx.x == 0) bad = 0;
-    __syncthreads();
-    for (int j = 0; j < n; ++j) {
-        double* cj = B + (long long)j * (bw + 1);
-        const int w = min(bw, n - 1 - j);
-        if (threadIdx.x == 0) {
-            const double a = cj[0];
-            if (!(a > 0.0)) bad = 1;
-            const double d = a > 0.0 ? sqrt(a) : 1.0;
-            cj[0] = 1.0 / d;
-            colj[0] = d;
-        }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    for (int j0 = 0; j0 < n; j0 += kPanel) {
+        const int nb = min(kPanel, n - j0);
+        for (int e = threadIdx.x; e < nb * (bw + 1); e += blockDim.x) pan[e] = B[(long long)j0 * cs + e];
         __syncthreads();
+        // factor the panel in shared memory
+        for (int c = 0; c < nb; ++c) {
+            double* pc = pan + c * cs;
+            if (threadIdx.x == 0) {
+                const double a = pc[0];
+                if (!(a > 0.0)) bad = 1;
+                pc[0] = a > 0.0 ? sqrt(a) : 1.0;
+            }
+            __syncthreads();
+            if (bad) break;
+            const int w = min(bw, n - 1 - (j0 + c));
+            const double inv = 1.0 / pc[0];
+            for (int o = 1 + threadIdx.x; o <= w; o += blockDim.x) pc[o] *= inv;
+            __syncthreads();
+            // later panel columns c2: A(j0+c2+o2, j0+c2) -= L(j0+c2+o2, j0+c) L(j0+c2, j0+c)
+            for (int c2 = c + 1; c2 < nb; ++c2) {
+                const int d = c2 - c;
+                if (d > w) break;
+                const double l2 = pc[d];
+                double* p2 = pan + c2 * cs;
+                for (int o2 = threadIdx.x; o2 <= w - d; o2 += blockDim.x) p2[o2] -= pc[d + o2] * l2;
+            }
+            __syncthreads();
+        }
         if (bad) break;
-        const double inv = 1.0 / colj[0];
-        for (int t = 1 + threadIdx.x; t <= w; t += blockDim.x) {
-            const double v = cj[t] * inv;
-            cj[t] = v;
-            colj[t] = v;
+        for (int e = threadIdx.x; e < nb * (bw + 1); e += blockDim.x) {
+            const int c = e / (bw + 1), o = e - c * (bw + 1);
+            B[(long long)j0 * cs + e] = o == 0 ? 1.0 / pan[e] : pan[e];
         }
-        __syncthreads();
-        for (int l = 1 + threadIdx.x; l <= w; l += blockDim.x) {
-            const double cl = colj[l];
-            if (cl == 0.0) continue;
-            for (int k0 = 1; k0 <= l; k0 += 16) {
-                double v[16];
+        // rank-nb update of the trailing window
+        const int rmax = min(n - 1, j0 + nb - 1 + bw);
+        for (int cp = j0 + nb + warp; cp <= rmax; cp += nwarp) {
+            double lc[kPanel];
 #pragma unroll
-                for (int u = 0; u < 16; ++u) {
-                    const int k = k0 + u;
-                    if (k <= l) v[u] = B[(long long)(j + k) * (bw + 1) + (l - k)];
+            for (int c = 0; c < kPanel; ++c) {
+                const int o = cp - (j0 + c);
+                lc[c] = (c < nb && o <= bw) ? pan[c * cs + o] : 0.0;
+            }
+            double* col = B + (long long)cp * cs - cp;   // col[r] = A(r, cp)
+            for (int r0 = cp + lane; r0 <= rmax; r0 += 128) {
+                double v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int r = r0 + 32 * u;
+                    v[u] = r <= rmax ? col[r] : 0.0;
                 }
 #pragma unroll
-                for (int u = 0; u < 16; ++u) {
-                    const int k = k0 + u;
-                    if (k <= l) B[(long long)(j + k) * (bw + 1) + (l - k)] = v[u] - cl * colj[k];
+                for (int u = 0; u < 4; ++u) {
+                    const int r = r0 + 32 * u;
+                    if (r > rmax) break;
+                    double acc = 0.0;
+#pragma unroll
+                    for (int c = 0; c < kPanel; ++c) {
+                        const int o = r - (j0 + c);
+                        if (c < nb && o <= bw) acc += pan[c * cs + o] * lc[c];
+                    }
+                    col[r] = v[u] - acc;
                 }
             }
         }
@@ -326,7 +360,7 @@ cudaError_t launch_band_factor(const PatchDesc* pd, const int* plist, int npl, i
     k_band_assemble<<<dim3((max_n + 255) / 256, npl), 256, 0, st>>>(pd, plist, K64, band);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const size_t sm = sizeof(double) * (size_t)(max_bw + 1);
+    const size_t sm = sizeof(double) * (size_t)kPanel * (size_t)(max_bw + 1);
     if (sm > 48 * 1024) {
         e = cudaFuncSetAttribute(k_band_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
