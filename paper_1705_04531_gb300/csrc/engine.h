@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <chrono>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -55,6 +56,11 @@ int ieti_engine_merged(ieti_engine* E, int stage, std::vector<std::pair<ietidp_h
 float ieti_engine_timed_ms(ieti_engine* E);
 // pinned read-back buffer of at least n doubles (valid until the next call)
 int ieti_engine_readback(ieti_engine* E, size_t n, double** out);
+// runs `eager` (stream-ordered launches on the engine's stream, nothing read
+// back to the host inside) as segment `seg` of a tick: captured as a CUDA
+// graph on the second occurrence of the same (segment, jobs, phases) and
+// replayed from then on; kernel launch counts are replayed with it
+int ieti_engine_staged(ieti_engine* E, int seg, std::vector<EngineJob*>& jobs, const std::function<int()>& eager);
 // MG-MG-S jobs (handles with method IETIDP_METHOD_SADDLE), lockstep BPCG:
 // one iteration of every job (none DONE) / iterations until all are DONE
 int ieti_saddle_tick(ieti_engine* E, std::vector<EngineJob*>& jobs);

@@ -24,6 +24,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <cstdint>
+#include <functional>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -662,12 +663,12 @@ std::vector<uintptr_t> segment_key(ieti_engine* E, int seg, const std::vector<En
         k.push_back((uintptr_t)j->f);
         k.push_back((uintptr_t)j->u);
         k.push_back((uintptr_t)(j->phase == EngineJob::RECOVER ? j->it : 0));
+        k.push_back((uintptr_t)j->fresh);
     }
     return k;
 }
 
-int staged(ieti_engine* E, int seg, std::vector<EngineJob*>& jobs, const std::vector<size_t>& rbo) {
-    auto eager = [&]() { return segment(E, seg, jobs, rbo); };
+int staged_fn(ieti_engine* E, int seg, std::vector<EngineJob*>& jobs, const std::function<int()>& eager) {
     if (!graphs_enabled()) return eager();
     const auto key = segment_key(E, seg, jobs);
     auto it = E->graphs.find(key);
@@ -711,7 +712,15 @@ int staged(ieti_engine* E, int seg, std::vector<EngineJob*>& jobs, const std::ve
     return IETIDP_OK;
 }
 
+int staged(ieti_engine* E, int seg, std::vector<EngineJob*>& jobs, const std::vector<size_t>& rbo) {
+    return staged_fn(E, seg, jobs, [&]() { return segment(E, seg, jobs, rbo); });
+}
+
 }  // namespace
+
+int ieti_engine_staged(ieti_engine* E, int seg, std::vector<EngineJob*>& jobs, const std::function<int()>& eager) {
+    return staged_fn(E, seg, jobs, eager);
+}
 
 int ieti_engine_tick(ieti_engine* E, std::vector<EngineJob*>& jobs) {
     cudaStream_t st = E->st;

@@ -201,6 +201,17 @@ int ieti_saddle_tick(ieti_engine* E, std::vector<EngineJob*>& jobs) {
         for (EngineJob* j : jobs) {
             ietidp_handle* h = j->h;
             ieti_saddle_bufs* b = h->saddle;
+            const bool init = j->phase == EngineJob::INIT || j->phase == EngineJob::RESTART;
+            SolveArgs a = ieti_solve_args(h, MODE_KHAT, init ? b->rtu : b->qtu, init ? b->ru : b->qu, 0.0, 0, h->vst);
+            a.ncycles = h->opt.saddle_vcycles;
+            a.omega = b->omega;
+            A.emplace_back(h, a);
+            B.emplace_back(h, ieti_solve_args(h, MODE_SCHUR, h->vS, h->wS, 0.0, 0, h->vst));
+        }
+        CHK(ieti_engine_staged(E, 10, jobs, [&]() -> int {
+        for (EngineJob* j : jobs) {
+            ietidp_handle* h = j->h;
+            ieti_saddle_bufs* b = h->saddle;
             const long long nU = b->nU;
             if (j->phase == EngineJob::INIT || j->phase == EngineJob::RESTART) {
                 if (j->phase == EngineJob::INIT) {
@@ -239,10 +250,6 @@ int ieti_saddle_tick(ieti_engine* E, std::vector<EngineJob*>& jobs) {
                 SCU(launch_primal_restrict(h->d_pd, h->nrows, h->crow_patch, h->crow_local, h->phi, b->rtu, h->rloc,
                                            st));
                 count_launch(*j, 1);
-                SolveArgs a = ieti_solve_args(h, MODE_KHAT, b->rtu, b->ru, 0.0, 0, h->vst);
-                a.ncycles = h->opt.saddle_vcycles;
-                a.omega = b->omega;
-                A.emplace_back(h, a);
             } else {
                 // search directions: p = r + beta p (copies on the first step)
                 SaddleLin L = lin(b->sc + 0, b->sc + 1, 1.0);
@@ -266,12 +273,10 @@ int ieti_saddle_tick(ieti_engine* E, std::vector<EngineJob*>& jobs) {
                 SCU(launch_primal_restrict(h->d_pd, h->nrows, h->crow_patch, h->crow_local, h->phi, b->qtu, h->rloc,
                                            st));
                 count_launch(*j, 2);
-                SolveArgs a = ieti_solve_args(h, MODE_KHAT, b->qtu, b->qu, 0.0, 0, h->vst);
-                a.ncycles = h->opt.saddle_vcycles;
-                a.omega = b->omega;
-                A.emplace_back(h, a);
             }
         }
+        return IETIDP_OK;
+        }));
         long long n0 = nl;
         CHK(ieti_engine_merged(E, 0, A, &nl, true));
         g_kernel_launches += nl - n0;
@@ -280,6 +285,7 @@ int ieti_saddle_tick(ieti_engine* E, std::vector<EngineJob*>& jobs) {
             j->S.neumann_launches += 1;
         }
         // ---- between: primal block, B~ of the result, Dirichlet preconditioner input
+        CHK(ieti_engine_staged(E, 11, jobs, [&]() -> int {
         for (EngineJob* j : jobs) {
             ietidp_handle* h = j->h;
             ieti_saddle_bufs* b = h->saddle;
@@ -301,13 +307,15 @@ int ieti_saddle_tick(ieti_engine* E, std::vector<EngineJob*>& jobs) {
             }
             SCU(launch_bt(h->dual, b->tl, h->vS, 1, st));
             count_launch(*j, init ? 2 : 3);
-            B.emplace_back(h, ieti_solve_args(h, MODE_SCHUR, h->vS, h->wS, 0.0, 0, h->vst));
         }
+        return IETIDP_OK;
+        }));
         n0 = nl;
         CHK(ieti_engine_merged(E, 1, B, &nl, false));
         g_kernel_launches += nl - n0;
         for (EngineJob* j : jobs) j->S.launches += nl - n0;
         // ---- after: updates, next residual products, <r, r>_H --------------------
+        CHK(ieti_engine_staged(E, 12, jobs, [&]() -> int {
         for (size_t i = 0; i < jobs.size(); ++i) {
             EngineJob* j = jobs[i];
             ietidp_handle* h = j->h;
@@ -366,6 +374,8 @@ int ieti_saddle_tick(ieti_engine* E, std::vector<EngineJob*>& jobs) {
             SCU(cudaMemcpyAsync(hrb + 16 * i + 8, h->vst, sizeof(long long) * 8, cudaMemcpyDeviceToHost, st));
             count_launch(*j, 5);
         }
+        return IETIDP_OK;
+        }));
         SCU(cudaStreamSynchronize(st));
         const float msA = ieti_engine_timed_ms(E);
         auto t1 = std::chrono::steady_clock::now();

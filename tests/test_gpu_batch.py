@@ -123,11 +123,12 @@ def test_zero_load_gives_zero_solution(api, method):
     assert st["outer_it"] == 0
 
 
-def test_graph_replay_equals_eager(api):
+@pytest.mark.parametrize("method", ["dual", "saddle", "dmg"])
+def test_graph_replay_equals_eager(api, method):
     """The CUDA-graph replay of the per-iteration launches gives the same bits
-    as eager launches."""
+    as eager launches (MG-MG, MG-MG-S and D-MG ticks)."""
     dom = W.annulus_6x6(8, 3, grid=(3, 3))
-    sol = api.Solver(api.Problem(dom), precision="mixed")
+    sol = api.Solver(api.Problem(dom), precision="mixed", method=method)
     u1, st1 = sol.solve()
     u1 = u1.clone()
     os.environ["IETIDP_GRAPHS"] = "0"
