@@ -11,11 +11,14 @@
 // differ (Sec. 3.2: w = P z).  The band is stored by columns, lower part:
 // band[bandoff + j (bw+1) + (i - j)] = L(i, j) for j < i <= j + bw, and the
 // reciprocal 1 / L(j, j) in place of the diagonal (the solves multiply).
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 
 #include "kernels.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -60,29 +63,41 @@ __global__ void k_band_assemble(const PatchDesc* pd, const int* plist, const dou
     }
 }
 
-// right-looking band Cholesky by panels of kPanel columns, one CTA per patch.
-// A panel (its columns' band entries, already updated by every earlier panel)
-// is factored in shared memory, written back (reciprocal diagonal), and then
-// applied once to the trailing window as a rank-kPanel update: every entry
-// A(r, c') with c' past the panel and r <= last panel column + bw loses
-// sum_c L(r, c) L(c', c) over the panel columns c.  One warp per trailing
-// column, lanes over its rows (coalesced), four rows per lane in flight.
+// right-looking band Cholesky by panels of kPanel columns, one thread-block
+// cluster per patch.  Every CTA of the cluster loads the panel (its columns'
+// band entries, already updated by every earlier panel) and factors it in
+// shared memory -- the same arithmetic on the same data, so the copies agree
+// bit for bit; each CTA writes back its share of the panel (reciprocal
+// diagonal) and applies the panel to its share of the trailing window as a
+// rank-kPanel update: every entry A(r, c') with c' past the panel and
+// r <= last panel column + bw loses sum_c L(r, c) L(c', c) over the panel
+// columns c.  One warp per trailing column (round-robin over the cluster's
+// warps), lanes over its rows (coalesced), four rows per lane in flight.
+// Two cluster barriers per panel: after the loads (the panel is written back
+// below) and after the updates (the next panel reads them).  A non-positive
+// pivot sets the flag and continues with pivot 1, so that every CTA passes
+// every barrier.
 constexpr int kPanel = 8;
 
 __global__ void __launch_bounds__(256) k_band_cholesky(const PatchDesc* pd, const int* plist, double* band,
                                                        int* flags) {
     extern __shared__ double pan[];           // [kPanel][bw + 1]
     __shared__ int bad;
-    const PatchDesc& P = pd[plist[blockIdx.x]];
+    cg::cluster_group cl = cg::this_cluster();
+    const int crank = (int)cl.block_rank(), csize = (int)cl.num_blocks();
+    const PatchDesc& P = pd[plist[blockIdx.x / csize]];
     const int n = P.n, bw = P.bw;
     const long long cs = bw + 1;
     double* B = band + P.bandoff;
     if (threadIdx.x == 0) bad = 0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int gwarp = crank * nwarp + warp, gnwarp = csize * nwarp;
     for (int j0 = 0; j0 < n; j0 += kPanel) {
         const int nb = min(kPanel, n - j0);
-        for (int e = threadIdx.x; e < nb * (bw + 1); e += blockDim.x) pan[e] = B[(long long)j0 * cs + e];
-        __syncthreads();
+        const int ne = nb * (bw + 1);
+        for (int e = threadIdx.x; e < ne; e += blockDim.x) pan[e] = B[(long long)j0 * cs + e];
+        __threadfence();
+        cl.sync();
         // factor the panel in shared memory
         for (int c = 0; c < nb; ++c) {
             double* pc = pan + c * cs;
@@ -92,7 +107,6 @@ __global__ void __launch_bounds__(256) k_band_cholesky(const PatchDesc* pd, cons
                 pc[0] = a > 0.0 ? sqrt(a) : 1.0;
             }
             __syncthreads();
-            if (bad) break;
             const int w = min(bw, n - 1 - (j0 + c));
             const double inv = 1.0 / pc[0];
             for (int o = 1 + threadIdx.x; o <= w; o += blockDim.x) pc[o] *= inv;
@@ -107,14 +121,16 @@ __global__ void __launch_bounds__(256) k_band_cholesky(const PatchDesc* pd, cons
             }
             __syncthreads();
         }
-        if (bad) break;
-        for (int e = threadIdx.x; e < nb * (bw + 1); e += blockDim.x) {
+        // this CTA's share of the panel back to the band
+        const int per = (ne + csize - 1) / csize;
+        const int e1 = min(ne, (crank + 1) * per);
+        for (int e = crank * per + threadIdx.x; e < e1; e += blockDim.x) {
             const int c = e / (bw + 1), o = e - c * (bw + 1);
             B[(long long)j0 * cs + e] = o == 0 ? 1.0 / pan[e] : pan[e];
         }
-        // rank-nb update of the trailing window
+        // rank-nb update of this CTA's share of the trailing window
         const int rmax = min(n - 1, j0 + nb - 1 + bw);
-        for (int cp = j0 + nb + warp; cp <= rmax; cp += nwarp) {
+        for (int cp = j0 + nb + gwarp; cp <= rmax; cp += gnwarp) {
             double lc[kPanel];
 #pragma unroll
             for (int c = 0; c < kPanel; ++c) {
@@ -143,9 +159,10 @@ __global__ void __launch_bounds__(256) k_band_cholesky(const PatchDesc* pd, cons
                 }
             }
         }
-        __syncthreads();
+        __threadfence();
+        cl.sync();
     }
-    if (threadIdx.x == 0 && bad) atomicOr(flags, IETI_FLAG_NOT_SPD);
+    if (threadIdx.x == 0 && crank == 0 && bad) atomicOr(flags, IETI_FLAG_NOT_SPD);
 }
 
 // (L L^T)^{-1} v in place, one CTA (v in shared or global memory).  Each
@@ -365,7 +382,23 @@ cudaError_t launch_band_factor(const PatchDesc* pd, const int* plist, int npl, i
         e = cudaFuncSetAttribute(k_band_cholesky, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
     }
-    k_band_cholesky<<<npl, 256, sm, st>>>(pd, plist, band, flags);
+    // CTAs per patch: enough warps that each takes a few trailing columns
+    // per panel (bw / 48: 4 for the annulus' 204, 8 for bands of 396 and up)
+    const int csize = std::max(1, std::min(8, max_bw / 48));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(npl * csize));
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)csize;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, k_band_cholesky, pd, plist, band, flags);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

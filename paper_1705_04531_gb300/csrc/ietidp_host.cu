@@ -994,12 +994,16 @@ extern "C" int ietidp_setup(const iga_problem* P, const ietidp_options* opt_in, 
     if (opt.method == IETIDP_METHOD_DMG) {
         std::vector<int> plist(N);
         int max_n = 0;
+        // IETIDP_DIRECT_SMEM=0 keeps every substitution vector in global
+        // memory (the path of patches above the shared-memory cap; for its tests)
+        const char* ds = std::getenv("IETIDP_DIRECT_SMEM");
+        const bool dsmem = !(ds && ds[0] == '0');
         for (int k = 0; k < N; ++k) {
             plist[k] = k;
             max_n = std::max(max_n, h->pd[k].n);
             h->max_bw = std::max(h->max_bw, h->pd[k].bw);
             const size_t zb = sizeof(double) * (size_t)h->pd[k].n;
-            if (zb <= kDirectSmemCap) h->direct_smem = std::max(h->direct_smem, zb);
+            if (dsmem && zb <= kDirectSmemCap) h->direct_smem = std::max(h->direct_smem, zb);
             // the band factorization costs n bw^2 per patch: kept for patches
             // where that stays moderate (2D patches; large 3D patches are
             // what the paper's direct variants could not hold either)

@@ -5,10 +5,15 @@ Dirichlet problems, through the C ABI against the CPU oracle's D-MG mode.
 Bars: relative solution error <= 1e-8 against the conforming direct solve
 (FP64 and mixed V-cycles in the preconditioner); outer iterations within +-1
 of the oracle's D-MG; batched = single; the factorization guard rejects a
-band too large to factor."""
+band too large to factor; the substitution vector in global memory (patches
+above the shared-memory cap) gives the same bits as in shared memory; bands
+wider than a CTA's threads (3D patches) take the strided sweep."""
+import os
+
 import numpy as np
 import pytest
 
+from oracle import assembly
 from oracle import ietidp as O
 from oracle.domain import Multipatch
 from paper_1705_04531_gb300 import workloads as W
@@ -72,3 +77,46 @@ def test_dmg_rejects_oversized_band(api):
     with pytest.raises(api.IetidpError) as e:
         api.Solver(prob, method="dmg")
     assert api.ERRORS[e.value.code] == "INVALID_ARG"
+
+
+def test_dmg_global_vector_path_equals_shared(api):
+    dom = DOMS["annulus3x3"]()
+    prob = api.Problem(dom)
+    u1, st1 = api.Solver(prob, precision="mixed", method="dmg").solve()
+    u1 = u1.clone()
+    os.environ["IETIDP_DIRECT_SMEM"] = "0"
+    try:
+        u0, st0 = api.Solver(prob, precision="mixed", method="dmg").solve()
+    finally:
+        del os.environ["IETIDP_DIRECT_SMEM"]
+    assert torch.equal(u0, u1)
+    assert st0["outer_it"] == st1["outer_it"]
+
+
+def test_dmg_wide_band_3d(api):
+    """2x2x2 cube, p=2, 16^3 elements per patch: 18^3 = 5832 functions and a
+    band of 2 + 18 (2 + 18 * 2) = 686 offsets, more than the 512 threads of a
+    solve.  Checked by continuity of the torn copies and by sampled interior
+    rows of the conforming system computed one by one by the oracle."""
+    dom = W.random_quad_rhs(W.cube_2x2x2(16, 2), seed=45)
+    sol = api.Solver(api.Problem(dom), precision="mixed", method="dmg")
+    u, st = sol.solve()
+    assert st["converged"]
+    got = sol.split(u)
+    mp = Multipatch(dom)
+    hi = np.full(mp.nglob, -np.inf)
+    lo = np.full(mp.nglob, np.inf)
+    for k, uk in enumerate(got):
+        np.maximum.at(hi, mp.l2g[k], uk)
+        np.minimum.at(lo, mp.l2g[k], uk)
+    assert np.max(hi - lo) <= 1e-9 * np.max(np.abs(hi))
+    rng = np.random.default_rng(1)
+    m = 18
+    for k in (0, 3, 7):
+        for _ in range(4):
+            i0, i1, i2 = (int(rng.integers(1, m - 1)) for _ in range(3))
+            i = i0 + m * (i1 + m * i2)
+            cols, vals, fi = assembly.row_stiffness_load(dom, k, i)
+            ku = float(vals @ got[k][cols])
+            scale = float(np.abs(vals) @ np.abs(got[k][cols])) + abs(fi)
+            assert abs(ku - fi) <= 1e-9 * scale, (k, i, ku, fi)
