@@ -401,7 +401,7 @@ def run_profile(args):
     from paper_1705_04531_gb300 import ietidp as api
     dom = workload(args.workload)
     probs = [api.Problem(dom) for _ in range(args.batch)]
-    sols = [api.Solver(p, precision=args.precision) for p in probs]
+    sols = [api.Solver(p, precision=args.precision, method=args.method) for p in probs]
     api.Solver.solve_batch(sols)
     torch.cuda.synchronize()
     torch.cuda.profiler.start()
@@ -412,7 +412,8 @@ def run_profile(args):
     its = sum(st["inner_its"] for st in sts)
     nl = sts[0]["neumann_launches"]
     print(json.dumps({"mode": "profile", "workload": args.workload, "batch": args.batch,
-                      "precision": args.precision, "neumann_launches": nl,
+                      "precision": args.precision, "method": args.method, "outer_it": sts[0]["outer_it"],
+                      "neumann_launches": nl,
                       "cg_iterations_per_launch": its / max(1, nl),
                       "alg_bytes_per_cg_iteration": bytes_per_iteration(ne, p, 4 if args.precision == "mixed" else 8),
                       "autotune": api.autotune_table()}), flush=True)
