@@ -192,89 +192,142 @@ __device__ void band_solve_loop(const double* B, int n, int bw, double* v) {
     }
 }
 
-// Thread t-1 owns band offset t (t <= bw < blockDim).  One barrier per step:
-// thread 0 (offset 1) makes the last update of the next pivot's entry, so it
-// also finishes that pivot (multiplies by the stored reciprocal diagonal)
-// and publishes it in the other half of a double buffer.  The factor entries
-// of the step four ahead (and, for thread 0, the reciprocal diagonals) are
-// loaded into register rings, so their L2 latency overlaps the steps before.
+// Blocked sweeps (bw < blockDim): pivots in blocks of four.  Per block one
+// CTA barrier: every thread k applies the block's four pivots to its row
+// (forward: row 4b+4+k, the column entries L(r, 4b+i); backward: row 4b-1-k,
+// the row entries L(4b+i, r), four consecutive doubles of column r), and
+// thread 0 -- after a warp barrier, since threads 0..3 of its warp own the
+// next block's rows -- solves the next block's 4x4 triangle and publishes
+// its pivots in the other half of a double buffer.  The factor entries of
+// the block four ahead (and, for thread 0, the triangle and reciprocal
+// diagonal of the block two ahead) are loaded into register rings, so their
+// latency overlaps the blocks before.
+struct Tri4 {
+    double l[6];   // L(1,0), L(2,0), L(3,0), L(2,1), L(3,1), L(3,2) of the block
+    double d[4];   // 1 / L(i,i)
+};
+
 __device__ void band_solve(const double* B, int n, int bw, double* v) {
     if (n <= 0) return;
     if (bw >= (int)blockDim.x) {              // more band offsets than threads
         band_solve_loop(B, n, bw, v);
         return;
     }
-    __shared__ double piv[2];
-    const int t = 1 + threadIdx.x;            // this thread's offset in the band (t <= bw)
-    const bool act = t <= bw;
-    const bool lead = threadIdx.x == 0;
+    __shared__ double piv[2][4];
+    const int k = threadIdx.x;
+    const bool lead = threadIdx.x == 0, warp0 = threadIdx.x < 32;
     const long long cs = bw + 1;
-    auto fwd_entry = [&](int j) -> double {   // L(j + t, j)
-        return (act && j < n && t <= n - 1 - j) ? B[(long long)j * cs + t] : 0.0;
+    const int nblk = (n + 3) / 4;
+    auto fE = [&](int b, int i) -> double {   // L(4b+4+k, 4b+i)
+        const int c = 4 * b + i, r = c + 4 + k - i;
+        return (b >= 0 && b < nblk && c < n && r < n && 4 + k - i <= bw) ? B[(long long)c * cs + (4 + k - i)] : 0.0;
     };
-    auto bwd_entry = [&](int j) -> double {   // L(j, j - t)
-        return (act && j >= 0 && t <= j) ? B[(long long)(j - t) * cs + t] : 0.0;
+    auto gE = [&](int b, int i) -> double {   // L(4b+i, 4b-1-k)
+        const int c = 4 * b - 1 - k, r = 4 * b + i;
+        return (b >= 0 && c >= 0 && r < n && i + 1 + k <= bw) ? B[(long long)c * cs + (i + 1 + k)] : 0.0;
     };
-    auto rdiag = [&](int j) -> double {       // 1 / L(j, j), thread 0 only
-        return (lead && j >= 0 && j < n) ? B[(long long)j * cs] : 0.0;
+    auto load_tri = [&](int b, Tri4& T) {
+        const int j0 = 4 * b;
+        const bool ok = lead && b >= 0 && b < nblk;
+        auto e = [&](int i, int i2) -> double {   // L(j0+i, j0+i2)
+            return (ok && j0 + i < n && i - i2 <= bw) ? B[(long long)(j0 + i2) * cs + (i - i2)] : 0.0;
+        };
+        T.l[0] = e(1, 0);
+        T.l[1] = e(2, 0);
+        T.l[2] = e(3, 0);
+        T.l[3] = e(2, 1);
+        T.l[4] = e(3, 1);
+        T.l[5] = e(3, 2);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) T.d[i] = (ok && j0 + i < n) ? B[(long long)(j0 + i) * cs] : 0.0;
     };
-    double ring[4], dring[4];
+    auto fwd_tri = [&](int b, const Tri4& T, double* pv) {   // thread 0
+        const int j0 = 4 * b, m = min(4, n - j0);
+        const double x0 = v[j0] * T.d[0];
+        const double x1 = m > 1 ? (v[j0 + 1] - T.l[0] * x0) * T.d[1] : 0.0;
+        const double x2 = m > 2 ? (v[j0 + 2] - T.l[1] * x0 - T.l[3] * x1) * T.d[2] : 0.0;
+        const double x3 = m > 3 ? (v[j0 + 3] - T.l[2] * x0 - T.l[4] * x1 - T.l[5] * x2) * T.d[3] : 0.0;
+        const double x[4] = {x0, x1, x2, x3};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if (i < m) v[j0 + i] = x[i];
+            pv[i] = x[i];
+        }
+    };
+    auto bwd_tri = [&](int b, const Tri4& T, double* pv) {   // thread 0
+        const int j0 = 4 * b, m = min(4, n - j0);
+        const double x3 = m > 3 ? v[j0 + 3] * T.d[3] : 0.0;
+        const double x2 = m > 2 ? (v[j0 + 2] - T.l[5] * x3) * T.d[2] : 0.0;
+        const double x1 = m > 1 ? (v[j0 + 1] - T.l[3] * x2 - T.l[4] * x3) * T.d[1] : 0.0;
+        const double x0 = (v[j0] - T.l[0] * x1 - T.l[1] * x2 - T.l[2] * x3) * T.d[0];
+        const double x[4] = {x0, x1, x2, x3};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if (i < m) v[j0 + i] = x[i];
+            pv[i] = x[i];
+        }
+    };
+    double e[4][4];
+    Tri4 T[2];
+    // ---- L y = v --------------------------------------------------------------
+#pragma unroll
     for (int u = 0; u < 4; ++u) {
-        ring[u] = fwd_entry(u);
-        dring[u] = rdiag(u + 1);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) e[u][i] = fE(u, i);
     }
-    if (lead) {
-        const double s0 = v[0] * B[0];
-        v[0] = s0;
-        piv[0] = s0;
-    }
+    load_tri(0, T[0]);
+    load_tri(1, T[1]);
+    if (lead) fwd_tri(0, T[0], piv[0]);
+    load_tri(2, T[0]);
     __syncthreads();
-    for (int j0 = 0; j0 < n; j0 += 4) {       // L y = v
+    for (int b0 = 0; b0 < nblk; b0 += 4) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const int j = j0 + u;
-            if (j >= n) break;
-            const double s = piv[j & 1];
-            const double lj = ring[u];
-            ring[u] = fwd_entry(j + 4);
-            if (lj != 0.0) v[j + t] -= lj * s;
-            if (lead) {
-                if (j + 1 < n) {
-                    const double sn = v[j + 1] * dring[u];
-                    v[j + 1] = sn;
-                    piv[(j + 1) & 1] = sn;
-                }
-                dring[u] = rdiag(j + 5);
+            const int b = b0 + u;
+            if (b >= nblk) break;
+            const double* s = piv[u & 1];
+            const double acc = e[u][0] * s[0] + e[u][1] * s[1] + e[u][2] * s[2] + e[u][3] * s[3];
+            const int r = 4 * b + 4 + k;
+            if (r < n && acc != 0.0) v[r] -= acc;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) e[u][i] = fE(b + 4, i);
+            if (warp0) {
+                __syncwarp();
+                const int un = (u + 1) & 1;
+                if (lead && b + 1 < nblk) fwd_tri(b + 1, T[un], piv[un]);
+                load_tri(b + 3, T[un]);
             }
             __syncthreads();
         }
     }
+    // ---- L^T x = y (blocks from the last) ---------------------------------------
+    const int bl = nblk - 1;
+#pragma unroll
     for (int u = 0; u < 4; ++u) {
-        ring[u] = bwd_entry(n - 1 - u);
-        dring[u] = rdiag(n - 2 - u);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) e[u][i] = gE(bl - u, i);
     }
-    if (lead) {
-        const double s0 = v[n - 1] * B[(long long)(n - 1) * cs];
-        v[n - 1] = s0;
-        piv[(n - 1) & 1] = s0;
-    }
+    load_tri(bl, T[0]);
+    load_tri(bl - 1, T[1]);
+    if (lead) bwd_tri(bl, T[0], piv[0]);
+    load_tri(bl - 2, T[0]);
     __syncthreads();
-    for (int j0 = n - 1; j0 >= 0; j0 -= 4) {  // L^T x = y
+    for (int q0 = 0; q0 < nblk; q0 += 4) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            const int j = j0 - u;
-            if (j < 0) break;
-            const double s = piv[j & 1];
-            const double lj = ring[u];
-            ring[u] = bwd_entry(j - 4);
-            if (lj != 0.0) v[j - t] -= lj * s;
-            if (lead) {
-                if (j >= 1) {
-                    const double sn = v[j - 1] * dring[u];
-                    v[j - 1] = sn;
-                    piv[(j - 1) & 1] = sn;
-                }
-                dring[u] = rdiag(j - 5);
+            const int b = bl - (q0 + u);
+            if (b < 0) break;
+            const double* s = piv[u & 1];
+            const double acc = e[u][0] * s[0] + e[u][1] * s[1] + e[u][2] * s[2] + e[u][3] * s[3];
+            const int r = 4 * b - 1 - k;
+            if (r >= 0 && acc != 0.0) v[r] -= acc;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) e[u][i] = gE(b - 4, i);
+            if (warp0) {
+                __syncwarp();
+                const int un = (u + 1) & 1;
+                if (lead && b - 1 >= 0) bwd_tri(b - 1, T[un], piv[un]);
+                load_tri(b - 3, T[un]);
             }
             __syncthreads();
         }
