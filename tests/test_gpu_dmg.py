@@ -7,7 +7,8 @@ Bars: relative solution error <= 1e-8 against the conforming direct solve
 of the oracle's D-MG; batched = single; the factorization guard rejects a
 band too large to factor; the substitution vector in global memory (patches
 above the shared-memory cap) gives the same bits as in shared memory; bands
-wider than a CTA's threads (3D patches) take the strided sweep."""
+wider than a CTA's threads (3D patches) take the strided sweep; the server
+with method D-MG gives each request the same result alone and in the mix."""
 import os
 
 import numpy as np
@@ -120,3 +121,22 @@ def test_dmg_wide_band_3d(api):
             ku = float(vals @ got[k][cols])
             scale = float(np.abs(vals) @ np.abs(got[k][cols])) + abs(fi)
             assert abs(ku - fi) <= 1e-9 * scale, (k, i, ku, fi)
+
+
+def test_dmg_server_alone_equals_mix(api):
+    """Serving with method D-MG: each request's result is the same alone and
+    in the mix (continuous batching) and equals the direct solve."""
+    reqs = [r.domain for r in W.serving_stream(nreq=4, rate=1000.0, seed=46, ms=(2, 3), ps=(2, 3), ns=(8, 16))]
+    srv = api.Server(8 << 30, max_concurrent=2, precision="mixed", method="dmg")
+    alone = []
+    for d in reqs:
+        state, u, st, tm = srv.wait(srv.submit(d))
+        assert st["converged"]
+        alone.append(u)
+    mixed = [srv.wait(t)[1] for t in [srv.submit(d) for d in reqs]]
+    srv.close()
+    for d, a, b in zip(reqs, alone, mixed):
+        assert np.linalg.norm(a - b) <= 1e-10 * np.linalg.norm(a)
+        mp = Multipatch(d)
+        ref = np.concatenate(mp.to_patches(mp.solve_global()))
+        assert np.linalg.norm(a - ref) <= 1e-8 * np.linalg.norm(ref)
