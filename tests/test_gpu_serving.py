@@ -1,4 +1,4 @@
-"""Continuous-batching server (spec serving pattern): requests of
+"""Continuous-batching server (the serving pattern): requests of
 different sizes, admitted by device-memory budget, overlap on the GPU; each
 result is the same alone and in the mix, and matches the oracle's direct
 solve."""
