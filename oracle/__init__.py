@@ -20,7 +20,13 @@ Everything here is plain, slow FP64 numpy/scipy written from the paper:
 * ``ietidp``    tearing, jump operator, primal constraints, energy-minimizing
                 primal basis (Eq. 6), local Neumann solves (Eq. 7), scaled
                 Dirichlet preconditioner and the dual PCG for Eq. 4, in the
-                D-D (direct) and MG-MG (multigrid) variants of Sec. 3.3.
+                D-D (direct), D-MG and MG-MG (multigrid) variants of Sec. 3.3.
+* ``saddle``    MG-MG-S: Bramble-Pasciak CG on the saddle-point system Eq. 2.
+* ``szcg``      the primal basis by Schoeberl-Zulehner preconditioned CG
+                (Sec. 3.2).
+* ``sharded``   the dual PCG with its patches sharded over ranks (the
+                exchange step of a multi-GPU solve: all-reduce of r_Pi and of
+                the partial jump-operator outputs).
 
 Parity status of each function is stated in its module header.
 """
