@@ -30,7 +30,12 @@ import sys
 import threading
 import time
 
-import numpy as np
+# the oracle legs (cpu_baseline, --impl reference) report one host core: the
+# BLAS / OpenMP pools are pinned to one thread before numpy loads them
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import numpy as np  # noqa: E402
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
