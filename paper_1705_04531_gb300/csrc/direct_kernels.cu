@@ -457,7 +457,8 @@ cudaError_t launch_band_factor(const PatchDesc* pd, const int* plist, int npl, i
 
 cudaError_t launch_direct_neumann(const SolveArgs& a, int max_bw, cudaStream_t st) {
     if (a.nslots == 0) return cudaSuccess;
-    // one thread per band offset (the solve's inner loops are unit-stride per step)
+    // one thread per band row past a pivot block (bw + 1 threads, rounded to
+    // warps; at most 512: wider bands take the strided sweep)
     const int threads = std::min(512, std::max(64, ((max_bw + 32) / 32) * 32));
     cudaError_t e = cudaFuncSetAttribute(k_direct_neumann, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kDirectSmemCap);
