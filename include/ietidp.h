@@ -196,6 +196,29 @@ void ietidp_default_options(ietidp_options* opt);
  * `out` receives a new problem; free it with iga_problem_free. */
 int iga_assemble_patches(const iga_domain_desc* dom, void* stream, iga_problem** out);
 
+/* Host-only topology of a domain, the first step of iga_assemble_patches
+ * (Sec. 2: the multipatch space, conforming interfaces, torn copies of the
+ * interface functions), run without any device work: the same validation of
+ * the descriptors (IETIDP_E_INVALID_ARG for a bad dimension, degree, box,
+ * patch index, side, a side used twice or a non-conforming interface) and
+ * the same identification of torn copies.
+ *   n_torn       sum over patches of the tensor-grid functions (n_r + p_r)
+ *   n_global     functions of the conforming space: n_torn minus, for every
+ *                class of identified copies, its size minus one (Dirichlet
+ *                functions included)
+ *   n_classes    classes of identified patch-boundary functions (size >= 1)
+ *   n_shared     classes with copies on two or more patches
+ *   n_dirichlet  classes on the Dirichlet boundary (a side of a patch that
+ *                has no interface)
+ *   n_floating   patches without a Dirichlet side
+ * `dmask` (host, npatch entries, may be NULL) receives per patch the bit
+ * mask of its Dirichlet sides (bit 2r: xi_r = 0, bit 2r+1: xi_r = 1). */
+typedef struct {
+    long long n_torn, n_global, n_classes, n_shared, n_dirichlet;
+    int n_floating;
+} iga_topology_info;
+int iga_topology(const iga_domain_desc* dom, iga_topology_info* info, unsigned* dmask);
+
 /* The assembled load vector f~ in patch layout (device, n_torn doubles). */
 int iga_problem_load(const iga_problem* prob, double* f_out);
 int iga_problem_free(iga_problem* prob);

@@ -209,6 +209,31 @@ static void local_coords(const iga_problem* P, int k, long long g, int* ii) {
 }
 
 // ---------------------------------------------------------------------------
+extern "C" int iga_topology(const iga_domain_desc* D, iga_topology_info* info, unsigned* dmask) {
+    if (!D || !info) return fail(IETIDP_E_INVALID_ARG, "null argument");
+    if (D->dim != 2 && D->dim != 3) return fail(IETIDP_E_INVALID_ARG, "dim must be 2 or 3");
+    if (D->npatch < 1 || !D->patches) return fail(IETIDP_E_INVALID_ARG, "no patches");
+    if (D->ninterface < 0 || (D->ninterface > 0 && !D->interfaces))
+        return fail(IETIDP_E_INVALID_ARG, "bad interface list");
+    iga_problem P;   // host part only: no device memory is allocated
+    int rc = build_topology(D, &P);
+    if (rc != IETIDP_OK) return rc;
+    std::memset(info, 0, sizeof(*info));
+    info->n_torn = P.ntorn;
+    info->n_global = P.ntorn;
+    info->n_classes = (long long)P.classes.size();
+    for (size_t c = 0; c < P.classes.size(); ++c) {
+        info->n_global -= (long long)P.classes[c].size() - 1;
+        if (P.classes[c].size() >= 2) info->n_shared += 1;
+        if (P.cls_dir[c]) info->n_dirichlet += 1;
+    }
+    for (int k = 0; k < P.npatch; ++k) {
+        if (P.dmask[k] == 0) info->n_floating += 1;
+        if (dmask) dmask[k] = (unsigned)P.dmask[k];
+    }
+    return IETIDP_OK;
+}
+
 extern "C" int iga_assemble_patches(const iga_domain_desc* D, void* stream, iga_problem** out) {
     if (!D || !out) return fail(IETIDP_E_INVALID_ARG, "null argument");
     *out = nullptr;

@@ -54,6 +54,11 @@ class iga_domain_desc(C.Structure):
                 ("quad_values", C.c_void_p)]
 
 
+class iga_topology_info(C.Structure):
+    _fields_ = [("n_torn", C.c_longlong), ("n_global", C.c_longlong), ("n_classes", C.c_longlong),
+                ("n_shared", C.c_longlong), ("n_dirichlet", C.c_longlong), ("n_floating", C.c_int)]
+
+
 class ietidp_options(C.Structure):
     _fields_ = [("primal", C.c_uint), ("precision", C.c_int), ("tol_outer", C.c_double),
                 ("tol_inner", C.c_double), ("tol_basis", C.c_double), ("maxit_outer", C.c_int),
@@ -86,6 +91,7 @@ class ietidp_info(C.Structure):
 _vp = C.c_void_p
 _SIGS = {
     "ietidp_default_options": (None, [C.POINTER(ietidp_options)]),
+    "iga_topology": (C.c_int, [C.POINTER(iga_domain_desc), C.POINTER(iga_topology_info), C.POINTER(C.c_uint)]),
     "iga_assemble_patches": (C.c_int, [C.POINTER(iga_domain_desc), _vp, C.POINTER(_vp)]),
     "iga_problem_load": (C.c_int, [_vp, _vp]),
     "iga_problem_free": (C.c_int, [_vp]),
@@ -221,6 +227,16 @@ def default_options(**kw) -> ietidp_options:
 
 
 # ---- C-named entry points ----------------------------------------------------
+def iga_topology(desc):
+    """Host-only topology of a domain descriptor (``domain_desc(dom)[0]`` or a
+    hand-made ``iga_domain_desc``): (counts as a dict, Dirichlet side masks)."""
+    info = iga_topology_info()
+    dm = (C.c_uint * max(1, desc.npatch))()
+    _check(_lib.iga_topology(C.byref(desc), C.byref(info), dm))
+    out = {f: getattr(info, f) for f, _ in iga_topology_info._fields_}
+    return out, [int(dm[k]) for k in range(desc.npatch)]
+
+
 def iga_assemble_patches(dom: W.Domain, stream=None):
     desc, keep = domain_desc(dom)
     h = C.c_void_p()
