@@ -4,11 +4,14 @@
  * The library solves the model problem of Eq. 1 (-Laplace u = f in Omega,
  * u = 0 on the boundary, a(u,v) = <F,v>) discretized with B-splines on a
  * multipatch domain (Sec. 2) by the dual-primal tearing and interconnecting
- * method with an energy-minimizing primal space, in the MG-MG variant of
- * Sec. 3.3: every local problem (the S-orthogonal primal basis of Eq. 6, the
- * local Neumann problems of Eq. 7 inside F = B K~^{-1} B^T, and the local
- * Dirichlet problems of the scaled Dirichlet preconditioner of Sec. 2/3.1)
- * is solved by geometric multigrid on the GPU.
+ * method with an energy-minimizing primal space.  Default: the MG-MG
+ * variant of Sec. 3.3, in which every local problem (the S-orthogonal primal
+ * basis of Eq. 6, the local Neumann problems of Eq. 7 inside
+ * F = B K~^{-1} B^T, and the local Dirichlet problems of the scaled
+ * Dirichlet preconditioner of Sec. 2/3.1) is solved by geometric multigrid
+ * on the GPU.  ietidp_options.method selects MG-MG-S (Bramble-Pasciak CG on
+ * the saddle-point system Eq. 2) or D-MG (direct banded-Cholesky Neumann
+ * solves, multigrid Dirichlet problems) instead.
  *
  * Conventions shared by every entry point:
  *  - return value: 0 on success, a negative IETIDP_E_* code on failure;
