@@ -106,6 +106,9 @@ struct SlotGroup {        // slots served by one kernel specialisation
 constexpr size_t kSmemCap = kSolveSmemCap;   // dynamic shared memory per CTA
 
 struct ietidp_handle {
+    // unique for the life of the process (a freed handle's address can be
+    // reused by the next one; captured launch graphs are keyed by this)
+    unsigned long long serial = 0;
     const iga_problem* prob = nullptr;
     ietidp_options opt;
     cudaStream_t st = nullptr;

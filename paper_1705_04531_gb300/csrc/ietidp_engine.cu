@@ -659,6 +659,7 @@ std::vector<uintptr_t> segment_key(ieti_engine* E, int seg, const std::vector<En
     k.push_back((uintptr_t)E->h_rb);
     for (EngineJob* j : jobs) {
         k.push_back((uintptr_t)j->h);
+        k.push_back((uintptr_t)j->h->serial);   // the address alone may be a recycled handle's
         k.push_back((uintptr_t)j->phase);
         k.push_back((uintptr_t)j->f);
         k.push_back((uintptr_t)j->u);

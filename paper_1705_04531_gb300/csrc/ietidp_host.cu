@@ -557,7 +557,9 @@ extern "C" int ietidp_setup(const iga_problem* P, const ietidp_options* opt_in, 
         (opt.basis_method != IETIDP_BASIS_SZ && opt.basis_method != IETIDP_BASIS_NULLSPACE))
         return fail(IETIDP_E_INVALID_ARG, "bad method options");
     auto t0 = std::chrono::steady_clock::now();
+    static std::atomic<unsigned long long> g_serial{0};
     auto* h = new ietidp_handle();
+    h->serial = ++g_serial;
     h->prob = P;
     h->opt = opt;
     h->st = (cudaStream_t)stream;
