@@ -680,6 +680,9 @@ int staged_fn(ieti_engine* E, int seg, std::vector<EngineJob*>& jobs, const std:
         ieti_host::g_kernel_launches += G.total;
         return IETIDP_OK;
     }
+    // occurrence counts of keys not captured yet: a server whose job mix keeps
+    // changing sees most keys once, so the table is bounded
+    if (it == E->graphs.end() && E->seen.size() >= 4096) E->seen.clear();
     if (it != E->graphs.end() || ++E->seen[key] < 2) return eager();
     if (E->graphs.size() >= 256) clear_graphs(E);
     auto G = std::make_unique<GraphEntry>();
