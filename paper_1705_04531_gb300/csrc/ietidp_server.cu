@@ -113,6 +113,10 @@ struct ietidp_server {
     bool stop = false;
     unsigned long long next_ticket = 1;
     std::vector<std::thread> workers;
+    // one stream per setup worker; a request's handle and problem stay
+    // ordered on it until the solve loop releases them, so the streams are
+    // destroyed only after the solve loop has ended
+    std::vector<cudaStream_t> wstreams;
     std::thread solver;
     int device = 0;
     int completed = 0;
@@ -141,20 +145,17 @@ void ietidp_server::release(const std::shared_ptr<Request>& r) {
 
 // setup workers: admit by budget, assemble and set up on the worker's own
 // stream, then hand the request to the solve loop
-void ietidp_server::worker(int /*wid*/) {
+void ietidp_server::worker(int wid) {
     cudaSetDevice(device);
     cudaStream_t st;
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return;
+    wstreams[wid] = st;
     for (;;) {
         std::shared_ptr<Request> r;
         {
             std::unique_lock<std::mutex> lk(mu);
             for (;;) {
-                if (stop) {
-                    lk.unlock();
-                    cudaStreamDestroy(st);
-                    return;
-                }
+                if (stop) return;   // the stream outlives the worker (see wstreams)
                 // first queued request that fits the budget
                 auto it = queue.begin();
                 for (; it != queue.end(); ++it) {
@@ -288,6 +289,7 @@ extern "C" int ietidp_server_create(long long budget_bytes, int max_concurrent, 
     if (opt) s->opt = *opt;
     else ietidp_default_options(&s->opt);
     cudaGetDevice(&s->device);
+    s->wstreams.assign(max_concurrent, nullptr);
     for (int i = 0; i < max_concurrent; ++i) s->workers.emplace_back([s, i] { s->worker(i); });
     s->solver = std::thread([s] { s->solve_loop(); });
     *out = s;
@@ -380,6 +382,9 @@ extern "C" int ietidp_server_destroy(ietidp_server* s) {
     s->cv.notify_all();
     for (auto& w : s->workers) w.join();
     s->solver.join();
+    // the solve loop has released every request: no handle uses these now
+    for (cudaStream_t st : s->wstreams)
+        if (st) cudaStreamDestroy(st);
     delete s;
     return IETIDP_OK;
 }
