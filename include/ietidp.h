@@ -26,7 +26,12 @@
  *    work of a handle is ordered on the stream given when it was created;
  *  - invalid descriptors are rejected before any device work; no entry point
  *    traps the device; iterative solvers that hit their iteration limit
- *    return IETIDP_E_NOT_CONVERGED with the statistics filled in.
+ *    return IETIDP_E_NOT_CONVERGED with the statistics filled in;
+ *  - a handle (and a problem) is used by one host thread at a time, and a
+ *    batch (ietidp_solve_batch*) uses every handle in it, launching on the
+ *    first handle's engine; different handles may be used from different
+ *    threads concurrently; a server's submit, poll, status and estimate may
+ *    be called from any thread, and ietidp_server_destroy after all of them.
  *
  * Torn vector layout ("patch layout"): patch after patch, each patch's
  * coefficients on its full tensor grid of (n_r + p_r) functions per

@@ -939,10 +939,16 @@ int run_jobs(ietidp_handle* const* hs, int n, std::vector<EngineJob>& jobs, bool
         for (int k = 0; k < i; ++k) dup = dup || hs[k]->st == hs[i]->st;
         if (dup) continue;
         cudaEvent_t ev;
-        CU(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-        evs.push_back(ev);
-        CU(cudaEventRecord(ev, hs[i]->st));
-        CU(cudaStreamWaitEvent(st, ev, 0));
+        cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) {
+            evs.push_back(ev);
+            e = cudaEventRecord(ev, hs[i]->st);
+        }
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev, 0);
+        if (e != cudaSuccess) {
+            cleanup();
+            return fail(IETIDP_E_CUDA, std::string("stream join: ") + cudaGetErrorString(e));
+        }
     }
     if (host)
         for (int i = 0; i < n; ++i)
