@@ -451,6 +451,14 @@ cudaError_t launch_band_factor(const PatchDesc* pd, const int* plist, int npl, i
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     e = cudaLaunchKernelEx(&cfg, k_band_cholesky, pd, plist, band, flags);
+    if (e != cudaSuccess && csize > 1) {
+        // clusters that cannot be co-scheduled (launch-configuration error,
+        // not sticky): one CTA per patch, the same arithmetic
+        cudaGetLastError();
+        cfg.gridDim = dim3((unsigned)npl);
+        attr[0].val.clusterDim.x = 1;
+        e = cudaLaunchKernelEx(&cfg, k_band_cholesky, pd, plist, band, flags);
+    }
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
