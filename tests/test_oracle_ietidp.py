@@ -132,3 +132,18 @@ def test_dmg_iterations_equal_mgmg(case):
     b = ietidp.IETIDP(dom, ietidp.Options(mode="mg"))
     b.solve()
     assert abs(a.stats.outer_it - b.stats.outer_it) <= 1
+
+
+def test_no_primal_dofs_on_a_strip():
+    """Degenerate case: a 3x1 strip with vertex primal constraints only has
+    every cross point on the Dirichlet boundary, so n_Pi = 0 and no patch
+    floats; K~ is then block diagonal and the method is plain tearing and
+    interconnecting.  The solution still equals the global direct solve."""
+    dom = W.random_quad_rhs(W.uniform_grid(2, (3, 1), 2, 8, W.UNIT, None, ("vertex",)), seed=9)
+    mp = Multipatch(dom)
+    ref = mp.to_patches(mp.solve_global())
+    for mode in ("direct", "mg"):
+        s = ietidp.IETIDP(dom, ietidp.Options(mode=mode))
+        u = s.solve()
+        assert s.nPi == 0 and not any(s.floating) and s.nlam > 0
+        assert s.stats.converged and _relerr(u, ref) < 1e-10
