@@ -484,6 +484,10 @@ def main():
     # batched FP64 path (comparison), then the batched mixed path (headline)
     bt64 = time_batch(api, torch, dom, "fp64", args, flush, stream)
     b64_err = max(relerr(bt64["sols"][i].split(bt64["us"][i]), u64h) for i in range(args.batch))
+    # every whole-job figure takes the slowest rank's time (all ranks call these)
+    ms64b = max_over_ranks(sum(bt64["ms"]), dist, "cuda")
+    ms64s = max_over_ranks(sum(ms64), dist, "cuda")
+    ms1s = max_over_ranks(sum(ms1), dist, "cuda")
     ach64, _, lms64, _ = roofline(bt64, dom, 8)
     close_batch(bt64)
     if dist:
@@ -513,7 +517,7 @@ def main():
         t = time.perf_counter()
         api.Solver.solve_batch_host(bt["sols"], fnp, unp)
         e2e_t.append(time.perf_counter() - t)
-    e2e_val = world * args.batch * len(e2e_t) / sum(e2e_t)
+    e2e_val = world * args.batch * len(e2e_t) / max_over_ranks(sum(e2e_t), dist, "cuda")
     achieved, alg_bytes_per_launch, launch_ms, nlaunch = roofline(bt, dom, 4)
     sts = bt["stats"]
     close_batch(bt)
@@ -522,8 +526,9 @@ def main():
     # preconditioner), batched mixed path on the same workload
     bs = time_batch(api, torch, dom, "mixed", args, flush, stream, method="saddle")
     saddle_err = max(relerr(bs["sols"][i].split(bs["us"][i]), u64h) for i in range(args.batch))
-    saddle = {"value": world * args.batch * args.steps / (sum(bs["ms"]) / 1e3),
-              "ms_per_step": sum(bs["ms"]) / args.steps,
+    ms_s = max_over_ranks(sum(bs["ms"]), dist, "cuda")
+    saddle = {"value": job_value(ms_s, world, args.batch, args.steps),
+              "ms_per_step": ms_s / args.steps,
               "outer_it": bs["stats"][-1][0]["outer_it"], "vcycles_per_solve": bs["stats"][-1][0]["vcycles"],
               "rel_err_vs_fp64_dual": saddle_err,
               "note": "MG-MG-S: Bramble-Pasciak CG on Eq. 2, mixed V-cycles, same batch and tolerance"}
@@ -533,8 +538,9 @@ def main():
     # problems), batched mixed path on the same workload
     bd = time_batch(api, torch, dom, "mixed", args, flush, stream, method="dmg")
     dmg_err = max(relerr(bd["sols"][i].split(bd["us"][i]), u64h) for i in range(args.batch))
-    dmg = {"value": world * args.batch * args.steps / (sum(bd["ms"]) / 1e3),
-           "ms_per_step": sum(bd["ms"]) / args.steps,
+    ms_d = max_over_ranks(sum(bd["ms"]), dist, "cuda")
+    dmg = {"value": job_value(ms_d, world, args.batch, args.steps),
+           "ms_per_step": ms_d / args.steps,
            "outer_it": bd["stats"][-1][0]["outer_it"], "setup_ms": bd["setup_ms"],
            "rel_err_vs_fp64_dual": dmg_err,
            "note": "D-MG: direct banded-Cholesky local Neumann solves, multigrid Dirichlet problems, same batch"}
@@ -573,20 +579,20 @@ def main():
                            f"solved in lockstep by ietidp_solve_batch",
                    "autotune": tune},
         "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
-        "single": {"value": world * args.steps / (sum(ms1) / 1e3), "ms_per_step": sum(ms1) / args.steps,
+        "single": {"value": job_value(ms1s, world, 1, args.steps), "ms_per_step": ms1s / args.steps,
                    "p50_ms": float(np.percentile(ms1, 50)), "p99_ms": float(np.percentile(ms1, 99)),
                    "note": "one solve at a time (latency: 36 CTAs on 152 SMs)"},
         "outer_it": sts[-1][0]["outer_it"], "inner_it_avg": sts[-1][0]["inner_it_avg"],
         "kappa": sts[-1][0]["kappa"],
         "setup_ms": setup_ms, "assemble_ms": assemble_ms,
-        "fp64": {"value": world * args.batch * args.steps / (sum(bt64["ms"]) / 1e3),
-                 "ms_per_step": sum(bt64["ms"]) / args.steps,
-                 "single_value": world * args.steps / (sum(ms64) / 1e3),
+        "fp64": {"value": job_value(ms64b, world, args.batch, args.steps),
+                 "ms_per_step": ms64b / args.steps,
+                 "single_value": job_value(ms64s, world, 1, args.steps),
                  "single_p50_ms": float(np.percentile(ms64, 50)),
                  "outer_it": st64[-1]["outer_it"], "inner_it_avg": st64[-1]["inner_it_avg"],
                  "setup_ms": setup64, "batch_vs_single_rel_err": b64_err,
                  "roofline_achieved_gbs": ach64, "launch_ms": lms64},
-        "mixed_over_fp64": sum(bt64["ms"]) / tot,
+        "mixed_over_fp64": ms64b / tot,
         "mg_mg_s": saddle,
         "d_mg": dmg,
         "vcycle_dofs_per_s": vcycle_dofs_s, "vcycle_ms": vc_ms,
