@@ -11,9 +11,10 @@ the exact rational quarter circle times a linear radius):
            circle with control points (1,0), (1,1), (0,1) and weights
            (1, 1/sqrt 2, 1).
 
-Pins (tests/test_oracle_geometry.py): |C| = 1 on the whole arc; the Jacobian
-against central differences; the annulus right-hand side against a finite
-difference Laplacian of the manufactured solution.
+Pins (tests/test_oracle_assembly.py): |C| = 1 on the whole arc and its
+derivative against central differences; the patch Jacobians of both maps
+against central differences of the maps; the annulus right-hand side against
+a finite difference Laplacian of the manufactured solution; the annulus area.
 """
 from __future__ import annotations
 

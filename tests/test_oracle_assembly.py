@@ -20,6 +20,21 @@ def test_circle_is_exact():
     assert np.allclose(dcy[1:-1], (a[1] - b[1]) / (2 * h), atol=1e-8)
 
 
+@pytest.mark.parametrize("dom", [W.annulus_6x6(4, 3, grid=(3, 2)), W.cube_2x2x2(2, 2)])
+def test_patch_jacobian_vs_differences(dom):
+    rng = np.random.default_rng(3)
+    h = 1e-6
+    for k in (0, dom.npatch - 1):
+        xi = rng.uniform(0.05, 0.95, (20, dom.dim))
+        _, J = geometry.patch_map(dom, k, xi)
+        for b in range(dom.dim):
+            e = np.zeros(dom.dim)
+            e[b] = h
+            Xp, _ = geometry.patch_map(dom, k, xi + e)
+            Xm, _ = geometry.patch_map(dom, k, xi - e)
+            assert np.allclose(J[:, :, b], (Xp - Xm) / (2 * h), atol=1e-8)
+
+
 def test_annulus_rhs_is_minus_laplacian():
     dom = W.annulus_6x6(4, 3)
     rng = np.random.default_rng(0)

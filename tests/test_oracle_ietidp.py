@@ -75,6 +75,54 @@ def test_edge_average_weights():
                 assert np.allclose(np.sort(nz), np.sort(w), atol=1e-15)
 
 
+def _open_knot_integrals(n, p):
+    """Integrals of the n+p B-splines of degree p on the open uniform knot
+    vector of n elements over (0,1): (t_{i+p+1} - t_i) / (p + 1)."""
+    t = np.concatenate([np.zeros(p + 1), np.arange(1, n) / n, np.ones(p + 1)])
+    return np.array([(t[i + p + 1] - t[i]) / (p + 1) for i in range(n + p)])
+
+
+def test_face_average_weights():
+    """3D face rows of C: the weight of the face function (j_a, j_b) is the
+    product of the two tangential 1D basis integrals over the face's interior
+    functions (the trace minus its edges), normalised to sum 1.  Every
+    direction has its own degree and element count, so that a wrong
+    tangential pair, a transposed pair or a missing normalisation changes the
+    expected weight of some position."""
+    degree = [[2, 2], [3, 3], [2]]
+    nelem = [[4, 4], [5, 5], [6]]
+    dom = W.Domain(3, (2, 2, 1), degree, nelem, W.UNIT, {"kind": "sin3d"},
+                   (W.PRIMAL_VERTEX, W.PRIMAL_EDGE, W.PRIMAL_FACE), "face_pin")
+    dom = W.random_quad_rhs(dom, seed=7)
+    s = ietidp.IETIDP(dom, ietidp.Options(mode="direct"))
+    m = [nelem[r][0] + degree[r][0] for r in range(3)]
+    ints = [_open_knot_integrals(nelem[r][0], degree[r][0]) for r in range(3)]
+    nface = 0
+    for k in range(s.N):
+        fr = s.free[k]
+        for row in s.C[k].toarray():
+            nzl = np.nonzero(row)[0]
+            if len(nzl) <= 1:
+                continue
+            full = fr[nzl]
+            ti = [full % m[0], (full // m[0]) % m[1], full // (m[0] * m[1])]
+            const = [r for r in range(3) if np.all(ti[r] == ti[r][0])]
+            if len(const) != 1:
+                continue                      # an edge row (two fixed directions)
+            nface += 1
+            normal = const[0]
+            assert ti[normal][0] in (0, m[normal] - 1)
+            tang = [r for r in range(3) if r != normal]
+            # the interior functions of the face, all of them present
+            for r in tang:
+                assert set(ti[r]) == set(range(1, m[r] - 1))
+            w = ints[tang[0]][ti[tang[0]]] * ints[tang[1]][ti[tang[1]]]
+            den = ints[tang[0]][1:-1].sum() * ints[tang[1]][1:-1].sum()
+            assert np.allclose(row[nzl], w / den, rtol=1e-14, atol=0)
+    # 2x2x1 grid: four interior faces, each seen from both of its patches
+    assert nface == 8
+
+
 def test_lanczos_kappa_matches_spectrum():
     dom = W.random_quad_rhs(W.square_2x2(8, 2))
     s = ietidp.IETIDP(dom, ietidp.Options(mode="direct", tol_outer=1e-14))
