@@ -294,21 +294,36 @@ long long ietidp_kernel_launches(void);
  * device vectors in patch layout.  Used to measure V-cycle throughput. */
 int ietidp_vcycles(ietidp_handle* h, const double* b, double* x, int ncycles);
 
+/* As ietidp_vcycles on a chosen hierarchy of every patch (Sec. 3.1, 3.2, 4):
+ * hierarchy 0 = the Neumann hierarchy (K, or K + alpha M^ on floating
+ * patches; Dirichlet sides masked), 1 = the Dirichlet hierarchy of the
+ * scaled Dirichlet preconditioner (K_II: every side masked).  Residuals use
+ * the FP64 fine K with the same mask; masked entries of x are left as they
+ * are.  Returns IETIDP_E_INVALID_ARG for another hierarchy value. */
+int ietidp_vcycles_hierarchy(ietidp_handle* h, int hierarchy, const double* b, double* x, int ncycles);
+
 /* Same V-cycles as ietidp_vcycles, but allocating nothing: for callers that
  * cannot allocate device memory when they run (a plugin inside a host
  * framework that owns the device memory pool, a latency-bound loop that must
  * not call cudaMalloc/cudaFree).  The paper has no counterpart; this is a
  * deployment variant of the V-cycle kernel.  The kernel's scratch vectors
  * (FP64 residual and correction, per-level vectors of every patch) live in
- * one static device array of 16 MiB per device, held by every device that
- * loads the library until the process exits.  The handle's device must be
- * current; the first call on a device looks up the array's address (with
- * that device current).  Problems whose scratch exceeds 16 MiB are rejected
- * with IETIDP_E_INVALID_ARG and a message giving both sizes.  All calls on a
- * device share the array and it keeps the last call's contents (the kernel
- * writes every scratch entry before reading it, so nothing needs clearing);
- * calls whose work overlaps on the GPU (other streams, other handles, other
- * host threads) race on it.  b, x as for ietidp_vcycles. */
+ * one static device array of 16 MiB per device.  ietidp_setup looks up the
+ * array's device address on the handle's device and keeps it in the handle;
+ * the array's memory is committed when the library's device code is loaded
+ * on that device: at the first CUDA call of the library under eager module
+ * loading, at that lookup in the first ietidp_setup under lazy loading (the
+ * CUDA 12+ default).  It is held until the process exits, or until the
+ * device's primary context is destroyed, which invalidates every handle of
+ * that device (set up new handles afterwards).  This call allocates nothing,
+ * does not modify the handle, and must be made with the handle's device
+ * current.  Problems whose scratch exceeds 16 MiB are rejected with
+ * IETIDP_E_INVALID_ARG and a message giving both sizes, before any device
+ * work.  All calls on a device share the array and it keeps the last call's
+ * contents (the kernel writes every scratch entry before reading it, so
+ * nothing needs clearing); calls whose work overlaps on the GPU (other
+ * streams, other handles, other host threads) race on it.  b, x as for
+ * ietidp_vcycles. */
 int ietidp_vcycles_noalloc(ietidp_handle* h, const double* b, double* x, int ncycles);
 
 /* Helpers exposed for testing the building blocks against the oracle:

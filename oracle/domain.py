@@ -112,11 +112,20 @@ class Multipatch:
         return Kg, fg
 
     def solve_global(self):
-        """Conforming Galerkin solution (global coefficients, 0 on Dirichlet)."""
+        """Conforming Galerkin solution (global coefficients, 0 on Dirichlet).
+
+        Sparse direct solve of the SPD system: LU without pivoting (none is
+        needed for SPD matrices) in a minimum-degree ordering of K + K^T,
+        which keeps the fill of million-dof 2D systems to minutes."""
         Kg, fg = self.global_system()
         fr = self.free
         u = np.zeros(self.nglob)
-        u[fr] = spla.spsolve(sp.csc_matrix(Kg[fr][:, fr]), fg[fr])
+        A = sp.csc_matrix(Kg[fr][:, fr])
+        if A.shape[0] == 0:
+            return u
+        lu = spla.splu(A, permc_spec="MMD_AT_PLUS_A", diag_pivot_thresh=0.0,
+                       options={"SymmetricMode": True})
+        u[fr] = lu.solve(fg[fr])
         return u
 
     def to_patches(self, u):

@@ -172,6 +172,7 @@ struct ietidp_handle {
     int device = 0;                 // device current at setup
     long long cg_patch_elems = 0;   // FP64 scratch used by the per-patch slots
     long long lv_patch_elems = 0;   // level-vector scratch used by the per-patch slots
+    void* noalloc_base = nullptr;   // device address of the static scratch of ietidp_vcycles_noalloc
     struct ieti_engine* engine = nullptr;   // solve engine on this handle's stream (created on first solve)
     struct ieti_saddle_bufs* saddle = nullptr;   // MG-MG-S vectors (created on first saddle solve)
 };

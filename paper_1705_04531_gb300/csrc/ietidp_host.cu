@@ -23,6 +23,10 @@
 #include "host_internal.h"
 #include "engine.h"
 
+// device address of the static scratch of ietidp_vcycles_noalloc on the
+// current device (defined with the array at the end of this file)
+static cudaError_t ieti_noalloc_address(void** p);
+
 // small vectors of one SZ basis slot (sz_device.cuh: kSmall)
 static constexpr long long ieti_sz_small() { return 64; }
 
@@ -474,10 +478,10 @@ SolveArgs ieti_solve_args(const ietidp_handle* h, int mode, const double* in, do
     return a;
 }
 
-static int run_solve(ietidp_handle* h, int mode, const std::vector<SlotGroup>& groups, const double* in,
-                     double* out, double tol, int maxit, long long* vst) {
-    SolveArgs a = ieti_solve_args(h, mode, in, out, tol, maxit, vst);
-    bool timed = mode == MODE_NEUMANN && h->nev_used + 2 <= (int)h->ev.size();
+// launch the slot groups with prepared kernel arguments on the handle's
+// stream (groups of different specialisations concurrently on side streams)
+static int run_solve_args(ietidp_handle* h, const SolveArgs& a, const std::vector<SlotGroup>& groups) {
+    bool timed = a.mode == MODE_NEUMANN && h->nev_used + 2 <= (int)h->ev.size();
     if (timed) cudaEventRecord(h->ev[h->nev_used], h->st);
     if (groups.size() == 1) {
         CHK(launch_group(h, a, groups[0], h->st));
@@ -499,6 +503,11 @@ static int run_solve(ietidp_handle* h, int mode, const std::vector<SlotGroup>& g
         h->nev_used += 2;
     }
     return IETIDP_OK;
+}
+
+static int run_solve(ietidp_handle* h, int mode, const std::vector<SlotGroup>& groups, const double* in,
+                     double* out, double tol, int maxit, long long* vst) {
+    return run_solve_args(h, ieti_solve_args(h, mode, in, out, tol, maxit, vst), groups);
 }
 
 static int make_groups(ietidp_handle* h, const std::vector<SlotDesc>& slots, std::vector<SlotGroup>& out,
@@ -588,6 +597,10 @@ extern "C" int ietidp_setup(const iga_problem* P, const ietidp_options* opt_in, 
     h->npatch = N;
     h->dim = d;
     CUH(cudaGetDevice(&h->device));
+    // address of the no-allocation V-cycle scratch on this device: looking it
+    // up here (where allocating is allowed) commits the array's memory under
+    // lazy module loading, so that ietidp_vcycles_noalloc never does
+    CUH(ieti_noalloc_address(&h->noalloc_base));
     // ---- primal objects and constraint rows -------------------------------
     // object kind of a class: number of directions in which its first copy
     // lies on the patch boundary
@@ -1222,11 +1235,17 @@ extern "C" int ietidp_phase_timers(ietidp_handle* h, long long* out64) {
 
 extern "C" int ietidp_vcycles(ietidp_handle* h, const double* b, double* x, int ncycles) {
     if (!h || !b || !x || ncycles < 0) return fail(IETIDP_E_INVALID_ARG, "bad argument");
-    ietidp_options save = h->opt;
-    h->opt.dirichlet_vcycles = ncycles;
-    int rc = run_solve(h, MODE_VCYCLE, h->gpatch, b, x, 0.0, 0, h->vst);
-    h->opt = save;
-    return rc;
+    SolveArgs a = ieti_solve_args(h, MODE_VCYCLE, b, x, 0.0, 0, h->vst);
+    a.ncycles = ncycles;
+    return run_solve_args(h, a, h->gpatch);
+}
+
+extern "C" int ietidp_vcycles_hierarchy(ietidp_handle* h, int hierarchy, const double* b, double* x, int ncycles) {
+    if (!h || !b || !x || ncycles < 0 || hierarchy < 0 || hierarchy > 1)
+        return fail(IETIDP_E_INVALID_ARG, "bad argument");
+    SolveArgs a = ieti_solve_args(h, hierarchy == 0 ? MODE_VCYCLE : MODE_VCYCLE_DIR, b, x, 0.0, 0, h->vst);
+    a.ncycles = ncycles;
+    return run_solve_args(h, a, h->gpatch);
 }
 
 extern "C" int ietidp_apply_K(ietidp_handle* h, const double* x, double* y) {
@@ -1300,24 +1319,29 @@ extern "C" int ietidp_destroy(ietidp_handle* h) {
 // and take unbounded time).  For them the scratch vectors of the V-cycle
 // kernel (the FP64 residual/correction vectors and the per-level vectors of
 // every patch) live in one file-scope device array of fixed size instead of
-// the handle's own buffers.  Its device address is looked up once per device
-// with that device current (the first call on a device does it); every call
-// on that device then shares the same array.
+// the handle's own buffers.  Host code cannot use the array's name as a
+// device address, so ietidp_setup looks the address up with
+// cudaGetSymbolAddress on the handle's device (with that device current) and
+// keeps it in the handle; under lazy module loading that lookup is also the
+// moment the array's memory is committed.  The call itself only reads the
+// kept address.  Every call on a device shares the same array.
 // ---------------------------------------------------------------------------
 namespace {
 constexpr size_t kNoAllocScratchBytes = 16u << 20;   // 16 MiB per device, held until exit
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
-constexpr int kNoAllocMaxDevices = 64;
-std::mutex g_noalloc_mu;
-void* g_noalloc_addr[kNoAllocMaxDevices] = {};
 }  // namespace
+
+static cudaError_t ieti_noalloc_address(void** p) {
+    *p = nullptr;
+    return cudaGetSymbolAddress(p, g_noalloc_scratch);
+}
 
 extern "C" int ietidp_vcycles_noalloc(ietidp_handle* h, const double* b, double* x, int ncycles) {
     if (!h || !b || !x || ncycles < 0) return fail(IETIDP_E_INVALID_ARG, "bad argument");
     int dev = -1;
     CU(cudaGetDevice(&dev));
     if (dev != h->device) return fail(IETIDP_E_INVALID_ARG, "the handle's device must be the current device");
-    if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(IETIDP_E_INVALID_ARG, "device ordinal out of range");
+    if (!h->noalloc_base) return fail(IETIDP_E_INVALID_ARG, "no static scratch address for this handle");
     const size_t tsz = h->opt.precision == IETIDP_PREC_MIXED ? sizeof(float) : sizeof(double);
     const size_t cg_bytes = ((size_t)h->cg_patch_elems * sizeof(double) + 255) & ~(size_t)255;
     const size_t need = cg_bytes + (size_t)h->lv_patch_elems * tsz;
@@ -1325,27 +1349,11 @@ extern "C" int ietidp_vcycles_noalloc(ietidp_handle* h, const double* b, double*
         return fail(IETIDP_E_INVALID_ARG, "problem needs " + std::to_string(need) +
                                               " bytes of V-cycle scratch; the static limit is " +
                                               std::to_string(kNoAllocScratchBytes) + " bytes");
-    void* base = nullptr;
-    {
-        std::lock_guard<std::mutex> lk(g_noalloc_mu);
-        if (!g_noalloc_addr[dev]) {
-            void* p = nullptr;
-            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-            if (e != cudaSuccess) return fail(IETIDP_E_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-            g_noalloc_addr[dev] = p;
-        }
-        base = g_noalloc_addr[dev];
-    }
-    // run the same V-cycle launch with the scratch pointers redirected
-    double* save_cg = h->cg;
-    void* save_lv = h->lv;
-    ietidp_options save = h->opt;
-    h->cg = (double*)base;
-    h->lv = (unsigned char*)base + cg_bytes;
-    h->opt.dirichlet_vcycles = ncycles;
-    int rc = run_solve(h, MODE_VCYCLE, h->gpatch, b, x, 0.0, 0, h->vst);
-    h->opt = save;
-    h->cg = save_cg;
-    h->lv = save_lv;
-    return rc;
+    // the regular V-cycle launch with its scratch pointers redirected in a
+    // local copy of the kernel arguments (the handle is not modified)
+    SolveArgs a = ieti_solve_args(h, MODE_VCYCLE, b, x, 0.0, 0, h->vst);
+    a.cg = (double*)h->noalloc_base;
+    a.lv = (unsigned char*)h->noalloc_base + cg_bytes;
+    a.ncycles = ncycles;
+    return run_solve_args(h, a, h->gpatch);
 }

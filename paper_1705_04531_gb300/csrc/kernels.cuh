@@ -98,7 +98,8 @@ enum SlotMode {
     MODE_KHAT = 5,
     MODE_SZW = 6,
     MODE_BASIS_SZ = 7,
-    MODE_NEUMANN_DIRECT = 8   // D-MG: Neumann solve by the banded Cholesky factor
+    MODE_NEUMANN_DIRECT = 8,  // D-MG: Neumann solve by the banded Cholesky factor
+    MODE_VCYCLE_DIR = 9       // V-cycles on the Dirichlet hierarchy (K_II, every side masked)
 };
 
 struct SolveArgs {

@@ -662,7 +662,7 @@ __global__ void __launch_bounds__(512) k_solve_t(SolveArgs a0) {
     double* p = z + n;
     double* q = p + n;
     const int allsides = D == 2 ? 0xF : 0x3F;
-    const int kind = (a.mode == MODE_SCHUR) ? 1 : 0;
+    const int kind = (a.mode == MODE_SCHUR || a.mode == MODE_VCYCLE_DIR) ? 1 : 0;
     const T* A0g = (a.mixed ? (const T*)(const void*)a.A0inv32 : (const T*)(const void*)a.A0inv64) + P.a0off[kind];
 
     const Plan pl = make_plan(P, sizeof(T), a.smem_bytes, !XG);
@@ -729,15 +729,16 @@ __global__ void __launch_bounds__(512) k_solve_t(SolveArgs a0) {
         return;
     }
 
-    if (a.mode == MODE_VCYCLE) {
+    if (a.mode == MODE_VCYCLE || a.mode == MODE_VCYCLE_DIR) {
         const double* bb = a.in + P.toff;
         double* xx = a.out + P.toff;
+        const int rmask = kind == 0 ? P.dmask : allsides;
         for (int c = 0; c < a.ncycles; ++c) {
-            spmv64<D, P0, P1, P2>(P, a.K64, xx, r, P.dmask, bb, -1.0, 0, a.phase);
+            spmv64<D, P0, P1, P2>(P, a.K64, xx, r, rmask, bb, -1.0, 0, a.phase);
             for (int i = threadIdx.x; i < n; i += blockDim.x) {
                 const int i0 = i % F.m[0], ir = i / F.m[0];
                 const int i1 = ir % F.m[1], i2 = ir / F.m[1];
-                if (ieti_masked(P.dmask, F.m, i0, i1, i2)) r[i] = 0.0;
+                if (ieti_masked(rmask, F.m, i0, i1, i2)) r[i] = 0.0;
             }
             __syncthreads();
             vcycle_apply(vc, r, z, a.nu1, a.nu2);

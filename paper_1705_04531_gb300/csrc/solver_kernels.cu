@@ -401,7 +401,7 @@ __global__ void __launch_bounds__(512) k_solve(SolveArgs a0) {
     double* p = z + n;
     double* q = p + n;
     const int allsides = P.dim == 2 ? 0xF : 0x3F;
-    const int kind = (a.mode == MODE_SCHUR) ? 1 : 0;
+    const int kind = (a.mode == MODE_SCHUR || a.mode == MODE_VCYCLE_DIR) ? 1 : 0;
 
     VCycle<T> vc;
     vc.P = &P;
@@ -579,13 +579,14 @@ __global__ void __launch_bounds__(512) k_solve(SolveArgs a0) {
         return;
     }
 
-    if (a.mode == MODE_VCYCLE) {
+    if (a.mode == MODE_VCYCLE || a.mode == MODE_VCYCLE_DIR) {
         const double* bb = a.in + P.toff;
         double* xx = a.out + P.toff;
+        const int rmask = kind == 0 ? P.dmask : allsides;
         for (int c = 0; c < a.ncycles; ++c) {
             for (int i = threadIdx.x; i < n; i += blockDim.x) {
                 int i0 = i % F.m[0], i1 = (i / F.m[0]) % F.m[1], i2 = i / (F.m[0] * F.m[1]);
-                r[i] = ieti_masked(P.dmask, F.m, i0, i1, i2) ? 0.0 : bb[i] - k64_row(P, a.K64, xx, i);
+                r[i] = ieti_masked(rmask, F.m, i0, i1, i2) ? 0.0 : bb[i] - k64_row(P, a.K64, xx, i);
             }
             __syncthreads();
             vcycle_apply(vc, r, z, a.nu1, a.nu2);

@@ -105,6 +105,7 @@ _SIGS = {
     "ietidp_autotune_table": (C.c_int, [_vp, C.c_int]),
     "ietidp_kernel_launches": (C.c_longlong, []),
     "ietidp_vcycles": (C.c_int, [_vp, _vp, _vp, C.c_int]),
+    "ietidp_vcycles_hierarchy": (C.c_int, [_vp, C.c_int, _vp, _vp, C.c_int]),
     "ietidp_vcycles_noalloc": (C.c_int, [_vp, _vp, _vp, C.c_int]),
     "ietidp_apply_K": (C.c_int, [_vp, _vp, _vp]),
     "ietidp_apply_F": (C.c_int, [_vp, _vp, _vp]),
@@ -382,6 +383,10 @@ class Solver:
 
     def vcycles(self, b, x, ncycles):
         _check(_lib.ietidp_vcycles(self.h, _ptr(b), _ptr(x), int(ncycles)))
+
+    def vcycles_hierarchy(self, hierarchy, b, x, ncycles):
+        """V-cycles on the Neumann (0) or Dirichlet (1) hierarchy of every patch."""
+        _check(_lib.ietidp_vcycles_hierarchy(self.h, int(hierarchy), _ptr(b), _ptr(x), int(ncycles)))
 
     def vcycles_noalloc(self, b, x, ncycles):
         """V-cycles whose scratch is the library's static device array (no

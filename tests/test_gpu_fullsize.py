@@ -3,13 +3,20 @@
 * quarter annulus 6x6, p=3, 64x64 elements per patch: the whole solution
   against the oracle's conforming direct solve (rel. error <= 1e-8), alone
   and as the benchmark's batch of 8 copies (MG-MG and MG-MG-S);
-* uneven 8x8 batch (degrees 2..4, 32..256 elements per direction) and the
-  2x2x2 cube (p=2, 32^3 elements per patch): too large for the oracle's
-  global solve, so sampled rows are checked one by one -- the oracle
-  computes single stiffness rows and load entries by quadrature, and the
-  GPU solution must satisfy K u = f on patch-interior rows -- and every
-  torn copy of an interface coefficient must agree (continuity, Eq. 2).
+* uneven 8x8 batch (degrees 2..4, 32..256 elements per direction, 1.55M
+  conforming dofs): the whole solution against the oracle's conforming
+  direct solve (rel. error <= 1e-8, both precisions; the host factorization
+  takes a few minutes);
+* uneven 8x8 batch and 2x2x2 cube (p=2, 32^3 elements per patch): sampled
+  rows checked one by one -- the oracle computes single stiffness rows and
+  load entries by quadrature, and the GPU solution must satisfy K u = f on
+  patch-interior rows -- and every torn copy of an interface coefficient
+  must agree (continuity, Eq. 2);
+* MG-MG-S iteration counts at the benchmark size against the oracle's FP64
+  count (tests/golden/bpcg_iterations_annulus6x6_p3_n64.txt).
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -98,6 +105,59 @@ def test_annulus_batch_of_8_as_benchmarked(api, annulus_ref, method):
         s_.close()
     for p in probs:
         p.close()
+
+
+@pytest.fixture(scope="module")
+def uneven_ref():
+    dom = W.uneven_8x8(0)
+    mp = Multipatch(dom)
+    return dom, mp.to_patches(mp.solve_global())
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_uneven_full_size_vs_global_solve(api, uneven_ref, prec):
+    dom, ref = uneven_ref
+    got, st = _solve(api, dom, prec)
+    err = np.sqrt(sum(np.sum((a - b) ** 2) for a, b in zip(got, ref)) / sum(np.sum(b ** 2) for b in ref))
+    assert st["converged"] and err <= 1e-8, err
+
+
+def _golden_counts():
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                        "bpcg_iterations_annulus6x6_p3_n64.txt")
+    out = {}
+    for ln in open(path):
+        if ln.strip() and not ln.startswith("#"):
+            k, v = ln.split()
+            out[k] = int(v)
+    return out
+
+
+def test_saddle_iterations_at_benchmark_size(api):
+    """FP64 BPCG within +-1 of the oracle's FP64 count; the mixed path
+    restarts from an FP64 residual after every 1e-4 of reduction (two
+    restarts at tolerance 1e-10), each of which may cost one iteration more
+    than the oracle's uninterrupted recursion, so it may take up to 2 + 1
+    more.  The dual PCG of MG-MG within +-1 of the oracle's."""
+    g = _golden_counts()
+    dom = W.annulus_6x6(64, 3)
+    prob = api.Problem(dom)
+    its = {}
+    for prec in ("fp64", "mixed"):
+        for method in ("saddle", "dual"):
+            sol = api.Solver(prob, precision=prec, method=method)
+            _, st = sol.solve()
+            assert st["converged"]
+            its[(prec, method)] = st["outer_it"]
+            sol.close()
+    prob.close()
+    print("iterations", its, "oracle", g)
+    ost = g["mg_mg_s_bpcg"]
+    restarts = 2
+    assert abs(its[("fp64", "saddle")] - ost) <= 1, (its, g)
+    assert ost - 1 <= its[("mixed", "saddle")] <= ost + 1 + restarts, (its, g)
+    for prec in ("fp64", "mixed"):
+        assert abs(its[(prec, "dual")] - g["mg_mg_dual_pcg"]) <= 1, (its, g)
 
 
 @pytest.mark.parametrize("name", ["uneven8x8", "cube2x2x2"])

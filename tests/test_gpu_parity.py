@@ -3,7 +3,8 @@
 Bars: assembled operators and loads to 1e-12 relative (same quadrature);
 primal basis to 1e-8; solutions to relative error <= 1e-8 against the
 conforming direct solve (FP64 and mixed paths); outer CG iterations within
-+-1 of the oracle's MG-MG mode.
++-1 of the oracle's MG-MG mode, and on the FP64 path the mean inner Neumann
+CG iteration count within +-1 of the oracle's.
 """
 import numpy as np
 import pytest
@@ -129,6 +130,12 @@ def test_solve_matches_oracle(api, name, prec):
     orc = O.IETIDP(dom, O.Options(mode="mg"))
     orc.solve()
     assert abs(st["outer_it"] - orc.stats.outer_it) <= 1, (st["outer_it"], orc.stats.outer_it)
+    if prec == "fp64":
+        # inner Neumann CG iterations (Eq. 7 solves of d, of every F apply and
+        # of the recovery), averaged over the solves with a non-zero
+        # right-hand side on both sides
+        its = [i for i in orc.stats.neumann_its if i > 0]
+        assert abs(st["inner_it_avg"] - np.mean(its)) <= 1.0, (st["inner_it_avg"], np.mean(its))
     # continuity: every pair of torn copies agrees
     unorm = np.sqrt(sum(np.sum(x ** 2) for x in got))
     jump = np.linalg.norm(orc.jump(got))

@@ -5,8 +5,9 @@ Bars: relative solution error <= 1e-8 against the conforming direct solve
 (FP64 and mixed V-cycles); BPCG iteration counts within +-1 of the oracle's
 MG-MG-S on the FP64 path; the mixed path restarts from an FP64 residual after
 every 1e-4 of reduction (refinement against the FP32 rounding of its
-V-cycles) and may take up to twice the oracle's count; batched and served
-results equal the single solves to rounding.
+V-cycles: two restarts at tolerance 1e-10) and may take one iteration fewer
+or up to one more per restart, plus one; batched and served results equal
+the single solves to rounding.
 """
 import numpy as np
 import pytest
@@ -60,10 +61,13 @@ def test_saddle_matches_direct_and_oracle(api, name, prec):
     if prec == "fp64":
         assert abs(st["outer_it"] - ost["iterations"]) <= 1, (st["outer_it"], ost["iterations"])
     else:
-        # FP32 V-cycles: the residual is recomputed in FP64 every 1e-4 of
-        # reduction (restarts), which costs some iterations
-        assert ost["iterations"] - 2 <= st["outer_it"] <= 2 * ost["iterations"] + 2, (st["outer_it"],
-                                                                                      ost["iterations"])
+        # FP32 V-cycles: the residual is recomputed in FP64 after every 1e-4
+        # of reduction (two restarts at tolerance 1e-10); each restart drops
+        # the recursion's history and may cost one iteration
+        restarts = 2
+        print(name, "mixed BPCG", st["outer_it"], "oracle FP64", ost["iterations"])
+        assert ost["iterations"] - 1 <= st["outer_it"] <= ost["iterations"] + 1 + restarts, (
+            st["outer_it"], ost["iterations"])
     assert st["vcycles"] > 0
 
 
