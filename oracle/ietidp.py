@@ -57,7 +57,7 @@ import scipy.linalg as sla
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
-from . import multigrid, splines
+from . import highorder, multigrid, splines
 from .domain import Multipatch
 
 
@@ -74,6 +74,11 @@ class Options:
     nu1: int = 2
     nu2: int = 2
     cmin: int = 4
+    # "standard": h-multigrid with Gauss-Seidel on every level (p fixed);
+    # "highorder": degree 1 below the finest level, L2-projection transfers
+    # and the subspace-corrected mass smoother on the finest level
+    # (oracle/highorder.py; Sec. 4, the setting of p >= 4)
+    mg_kind: str = "standard"
 
 
 @dataclass
@@ -295,8 +300,12 @@ class IETIDP:
                                     self.dom.patch_degree(k), o.cmin)
             self.hier.append(h)
             alpha = o.alpha if self.floating[k] else 0.0
-            self.mgN.append(multigrid.MGOperator(h, self.dmask[k], alpha, o.nu1, o.nu2))
-            self.mgD.append(multigrid.MGOperator(h, allsides, 0.0, o.nu1, o.nu2))
+            if o.mg_kind == "highorder":
+                self.mgN.append(highorder.HighOrderMG(self.dom, k, self.Kfull[k], self.dmask[k], alpha))
+                self.mgD.append(highorder.HighOrderMG(self.dom, k, self.Kfull[k], allsides, 0.0))
+            else:
+                self.mgN.append(multigrid.MGOperator(h, self.dmask[k], alpha, o.nu1, o.nu2))
+                self.mgD.append(multigrid.MGOperator(h, allsides, 0.0, o.nu1, o.nu2))
             self.phi.append(self._basis_mg(k))
 
     def _setup_mg_dirichlet(self):
@@ -307,7 +316,10 @@ class IETIDP:
         for k in range(self.N):
             h = multigrid.Hierarchy(self.Kfull[k], self.dom.patch_nelem(k), self.dom.patch_degree(k), o.cmin)
             self.hier.append(h)
-            self.mgD.append(multigrid.MGOperator(h, allsides, 0.0, o.nu1, o.nu2))
+            if o.mg_kind == "highorder":
+                self.mgD.append(highorder.HighOrderMG(self.dom, k, self.Kfull[k], allsides, 0.0))
+            else:
+                self.mgD.append(multigrid.MGOperator(h, allsides, 0.0, o.nu1, o.nu2))
 
     def _projector(self, k):
         C = self.C[k]
