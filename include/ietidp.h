@@ -294,6 +294,16 @@ long long ietidp_kernel_launches(void);
  * device vectors in patch layout.  Used to measure V-cycle throughput. */
 int ietidp_vcycles(ietidp_handle* h, const double* b, double* x, int ncycles);
 
+/* Batched form of ietidp_vcycles (Sec. 4 multigrid): the Neumann
+ * hierarchies of every patch of the n handles in one merged launch per
+ * kernel specialisation, x[i] <- x[i] + V(b[i] - A x[i]) for `ncycles`
+ * cycles.  b[i], x[i] are device vectors in handle i's patch layout; the
+ * handles must be distinct and on one device.  *ms_out (may be NULL)
+ * receives the duration of the merged launches (CUDA events; the first
+ * call of a launch shape includes its autotuning).  Synchronous. */
+int ietidp_vcycles_batch(ietidp_handle* const* hs, int n, const double* const* b, double* const* x, int ncycles,
+                         float* ms_out);
+
 /* As ietidp_vcycles on a chosen hierarchy of every patch (Sec. 3.1, 3.2, 4):
  * hierarchy 0 = the Neumann hierarchy (K, or K + alpha M^ on floating
  * patches; Dirichlet sides masked), 1 = the Dirichlet hierarchy of the

@@ -146,4 +146,22 @@ __host__ __device__ inline bool ieti_on_boundary(const int* m, int dim, int i0, 
 #define IETI_FLAG_TABLE         8
 #define IETI_FLAG_NOT_SPD      16
 
+// device clock in nanoseconds, common to every SM
+__device__ __forceinline__ unsigned long long ieti_gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// widens a launch's [start, end] span by this CTA's lifetime (thread 0)
+struct IetiLaunchSpan {
+    unsigned long long* p;
+    __device__ explicit IetiLaunchSpan(unsigned long long* q) : p(q) {
+        if (p && threadIdx.x == 0) atomicMin(p, ieti_gtimer());
+    }
+    __device__ ~IetiLaunchSpan() {
+        if (p && threadIdx.x == 0) atomicMax(p + 1, ieti_gtimer());
+    }
+};
+
 #define IETI_CUDA_CHECK(x) do { cudaError_t e_ = (x); if (e_ != cudaSuccess) return e_; } while (0)

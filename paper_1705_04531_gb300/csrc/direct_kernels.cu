@@ -354,6 +354,7 @@ __device__ double cta_sum1(double x, Red2& sh) {
 // solved directly (same input and output conventions as the multigrid
 // Neumann mode of the local solver)
 __global__ void __launch_bounds__(512) k_direct_neumann(SolveArgs a0) {
+    const IetiLaunchSpan span_(a0.tspan);
     extern __shared__ double zsh[];
     __shared__ SolveArgs sa;
     __shared__ double coef[64];

@@ -118,6 +118,7 @@ struct ietidp_handle {
     PatchDesc* d_pd = nullptr;
     double* K64 = nullptr;
     float* K32 = nullptr;
+    float* K32lo = nullptr;   // K - K32 rounded to FP32 (mixed path)
     double* KM64 = nullptr;   // K + alpha M^ on floating patches (same offsets as K64)
     float* KM32 = nullptr;
     double* tab = nullptr;

@@ -108,7 +108,10 @@ struct Staging {   // pinned and device copies of one launch stage's arguments a
 struct GraphEntry {   // one captured launch segment
     cudaGraphExec_t exec = nullptr;   // null: the segment could not be captured
     std::vector<long long> dl;        // per job: kernel launches of one replay
+    std::vector<long long> dn;        // per job: merged Neumann launches of one replay
     long long total = 0;              // kernels of one replay
+    void* d_args = nullptr;           // merged launch arguments and slots owned by the graph
+    void* d_slots = nullptr;
 };
 
 struct ieti_engine {
@@ -123,6 +126,7 @@ struct ieti_engine {
     Staging stA, stB, stT;
     double* h_rb = nullptr;   // pinned read-back, one block per job
     size_t cap_rb = 0;
+    unsigned long long* d_span = nullptr;   // [start, end] of the merged Neumann stage (globaltimer ns)
 };
 
 namespace {
@@ -155,8 +159,11 @@ void free_staging(ieti_engine* E, Staging& S) {
 }
 
 void clear_graphs(ieti_engine* E) {
-    for (auto& kv : E->graphs)
+    for (auto& kv : E->graphs) {
         if (kv.second->exec) cudaGraphExecDestroy(kv.second->exec);
+        if (kv.second->d_args) cudaFree(kv.second->d_args);
+        if (kv.second->d_slots) cudaFree(kv.second->d_slots);
+    }
     E->graphs.clear();
     E->seen.clear();
 }
@@ -288,9 +295,18 @@ int tune(ieti_engine* E, MGroup& g, const std::vector<ietidp_handle*>& hs, long 
     return IETIDP_OK;
 }
 
-// one local-solve stage: every item's slots, merged per specialisation
-int merged_launch(ieti_engine* E, Staging& S, std::vector<std::pair<ietidp_handle*, SolveArgs>>& items,
-                  long long* nlaunch) {
+// one local-solve stage prepared for launch: every item's slots, merged per
+// kernel specialisation (longest patches first), each group's launch shape
+// tuned, and the kernel arguments and slot lists as they go to the device
+struct MergedPrep {
+    std::vector<MGroup> groups;
+    std::vector<SolveArgs> args;    // per item
+    std::vector<SlotDesc> slots;    // the groups' slots, group after group
+};
+
+int merged_prepare(ieti_engine* E, std::vector<std::pair<ietidp_handle*, SolveArgs>>& items, MergedPrep& MP,
+                   long long* nlaunch) {
+    MP = MergedPrep{};
     if (items.empty()) return IETIDP_OK;
     std::map<std::tuple<int, int, int, int, int, int>, MGroup> by;
     for (size_t i = 0; i < items.size(); ++i) {
@@ -322,7 +338,6 @@ int merged_launch(ieti_engine* E, Staging& S, std::vector<std::pair<ietidp_handl
     }
     std::vector<ietidp_handle*> hs(items.size());
     for (size_t i = 0; i < items.size(); ++i) hs[i] = items[i].first;
-    size_t total = 0;
     for (auto& kv : by) {
         MGroup& m = kv.second;
         // longest patches first, so that uneven batches finish together
@@ -338,29 +353,31 @@ int merged_launch(ieti_engine* E, Staging& S, std::vector<std::pair<ietidp_handl
         m.s.swap(s2);
         m.cost.swap(c2);
         CHK(tune(E, m, hs, nlaunch));
-        total += m.s.size();
+        MP.slots.insert(MP.slots.end(), m.s.begin(), m.s.end());
+        MP.groups.push_back(std::move(m));
     }
-    CHK(reserve(E, S, items.size(), total));
-    for (size_t i = 0; i < items.size(); ++i) S.h_args[i] = items[i].second;
-    size_t off = 0;
-    for (auto& kv : by) {
-        std::copy(kv.second.s.begin(), kv.second.s.end(), S.h_slots + off);
-        off += kv.second.s.size();
-    }
-    CU(cudaMemcpyAsync(S.d_args, S.h_args, sizeof(SolveArgs) * items.size(), cudaMemcpyHostToDevice, E->st));
-    CU(cudaMemcpyAsync(S.d_slots, S.h_slots, sizeof(SlotDesc) * total, cudaMemcpyHostToDevice, E->st));
-    SolveArgs a0 = items[0].second;
-    a0.batch = S.d_args;
-    const bool multi = by.size() > 1;
+    for (auto& it : items) MP.args.push_back(it.second);
+    return IETIDP_OK;
+}
+
+// the launches of a prepared stage (groups of several specialisations run
+// concurrently on side streams); d_args / d_slots hold MP.args / MP.slots on
+// the device; tspan (or null): [first CTA start, last CTA end] in
+// globaltimer nanoseconds, widened by every launch of the stage
+int merged_issue(ieti_engine* E, const MergedPrep& MP, const SolveArgs* d_args, const SlotDesc* d_slots,
+                 unsigned long long* tspan, long long* nlaunch) {
+    if (MP.groups.empty()) return IETIDP_OK;
+    SolveArgs a0 = MP.args[0];
+    a0.batch = d_args;
+    a0.tspan = tspan;
+    const bool multi = MP.groups.size() > 1;
     if (multi) {
-        CHK(ensure_side(E, by.size()));
+        CHK(ensure_side(E, MP.groups.size()));
         CU(cudaEventRecord(E->fork, E->st));
     }
-    off = 0;
-    size_t gi = 0;
-    for (auto& kv : by) {
-        MGroup& m = kv.second;
-        a0.slots = S.d_slots + off;
+    size_t off = 0, gi = 0;
+    for (const MGroup& m : MP.groups) {
+        a0.slots = d_slots + off;
         a0.nslots = (int)m.s.size();
         a0.mixed = m.mixed;
         off += m.s.size();
@@ -375,12 +392,32 @@ int merged_launch(ieti_engine* E, Staging& S, std::vector<std::pair<ietidp_handl
         ++gi;
     }
     if (multi) {
-        for (size_t i = 0; i < std::min(by.size(), E->side.size()); ++i) {
+        for (size_t i = 0; i < std::min(MP.groups.size(), E->side.size()); ++i) {
             CU(cudaEventRecord(E->join[i], E->side[i]));
             CU(cudaStreamWaitEvent(E->st, E->join[i], 0));
         }
     }
     return IETIDP_OK;
+}
+
+// copy a prepared stage's arguments through the pinned staging buffers
+int merged_stage_copy(ieti_engine* E, Staging& S, const MergedPrep& MP) {
+    CHK(reserve(E, S, MP.args.size(), MP.slots.size()));
+    std::copy(MP.args.begin(), MP.args.end(), S.h_args);
+    std::copy(MP.slots.begin(), MP.slots.end(), S.h_slots);
+    CU(cudaMemcpyAsync(S.d_args, S.h_args, sizeof(SolveArgs) * MP.args.size(), cudaMemcpyHostToDevice, E->st));
+    CU(cudaMemcpyAsync(S.d_slots, S.h_slots, sizeof(SlotDesc) * MP.slots.size(), cudaMemcpyHostToDevice, E->st));
+    return IETIDP_OK;
+}
+
+// one local-solve stage, eager: prepare, copy, launch
+int merged_launch(ieti_engine* E, Staging& S, std::vector<std::pair<ietidp_handle*, SolveArgs>>& items,
+                  long long* nlaunch) {
+    if (items.empty()) return IETIDP_OK;
+    MergedPrep MP;
+    CHK(merged_prepare(E, items, MP, nlaunch));
+    CHK(merged_stage_copy(E, S, MP));
+    return merged_issue(E, MP, S.d_args, S.d_slots, nullptr, nlaunch);
 }
 
 double lanczos_kappa(const std::vector<double>& al, const std::vector<double>& be) {
@@ -490,6 +527,7 @@ int ieti_engine_create(cudaStream_t st, ieti_engine** out) {
     if (e == cudaSuccess) e = cudaEventCreate(&E->e1);
     if (e == cudaSuccess) e = cudaEventCreate(&E->t0);
     if (e == cudaSuccess) e = cudaEventCreate(&E->t1);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&E->d_span, 2 * sizeof(unsigned long long));
     if (e != cudaSuccess) {
         delete E;
         return fail(IETIDP_E_CUDA, std::string("engine events: ") + cudaGetErrorString(e));
@@ -507,6 +545,7 @@ void ieti_engine_destroy(ieti_engine* E) {
     free_staging(E, E->stT);
     cudaStreamSynchronize(E->st);
     if (E->h_rb) cudaFreeHost(E->h_rb);
+    if (E->d_span) cudaFree(E->d_span);
     for (auto s : E->side) cudaStreamDestroy(s);
     for (auto ev : E->join) cudaEventDestroy(ev);
     if (E->fork) cudaEventDestroy(E->fork);
@@ -604,44 +643,6 @@ int segment(ieti_engine* E, int seg, std::vector<EngineJob*>& jobs, const std::v
     return IETIDP_OK;
 }
 
-// merged local-solve launch of stage A (Neumann) or B (Dirichlet), eager;
-// stage A is bracketed by the engine's events
-int merged_stage(ieti_engine* E, int stage, std::vector<EngineJob*>& jobs) {
-    std::vector<std::pair<ietidp_handle*, SolveArgs>> items;
-    std::vector<EngineJob*> in;
-    for (EngineJob* j : jobs) {
-        ietidp_handle* h = j->h;
-        if (stage == 0) {
-            if (j->phase == EngineJob::INIT)
-                items.emplace_back(h, ieti_solve_args(h, MODE_NEUMANN, j->f, j->u, h->opt.tol_inner,
-                                                      h->opt.maxit_inner, h->vst));
-            else if (j->phase == EngineJob::ITER)
-                items.emplace_back(h, ieti_solve_args(h, MODE_NEUMANN, h->gF, h->uF, h->opt.tol_inner,
-                                                      h->opt.maxit_inner, h->vst));
-            else if (j->phase == EngineJob::RECOVER)
-                items.emplace_back(h, ieti_solve_args(h, MODE_NEUMANN, h->gR, j->u, h->opt.tol_inner,
-                                                      h->opt.maxit_inner, h->vst));
-            else
-                continue;
-        } else {
-            if (!in_B(j)) continue;
-            items.emplace_back(h, ieti_solve_args(h, MODE_SCHUR, h->vS, h->wS, 0.0, 0, h->vst));
-        }
-        in.push_back(j);
-    }
-    if (items.empty()) return IETIDP_OK;
-    long long nl = 0;
-    if (stage == 0) CU(cudaEventRecord(E->e0, E->st));
-    CHK(merged_launch(E, stage == 0 ? E->stA : E->stB, items, &nl));
-    if (stage == 0) CU(cudaEventRecord(E->e1, E->st));
-    ieti_host::g_kernel_launches += nl;
-    for (EngineJob* j : in) {
-        j->S.launches += nl;
-        if (stage == 0) j->S.neumann_launches += 1;
-    }
-    return IETIDP_OK;
-}
-
 // ---------------------------------------------------------------------------
 // CUDA graphs of the per-job launch segments: a segment whose launch sequence
 // repeats (same jobs, same phases: every steady-state outer iteration) is
@@ -716,8 +717,138 @@ int staged_fn(ieti_engine* E, int seg, std::vector<EngineJob*>& jobs, const std:
     return IETIDP_OK;
 }
 
-int staged(ieti_engine* E, int seg, std::vector<EngineJob*>& jobs, const std::vector<size_t>& rbo) {
-    return staged_fn(E, seg, jobs, [&]() { return segment(E, seg, jobs, rbo); });
+// the items of merged stage A (Neumann solves) or B (Dirichlet problems)
+void stage_items(int stage, std::vector<EngineJob*>& jobs, std::vector<std::pair<ietidp_handle*, SolveArgs>>& items,
+                 std::vector<size_t>& in) {
+    for (size_t i = 0; i < jobs.size(); ++i) {
+        EngineJob* j = jobs[i];
+        ietidp_handle* h = j->h;
+        if (stage == 0) {
+            if (j->phase == EngineJob::INIT)
+                items.emplace_back(h, ieti_solve_args(h, MODE_NEUMANN, j->f, j->u, h->opt.tol_inner,
+                                                      h->opt.maxit_inner, h->vst));
+            else if (j->phase == EngineJob::ITER)
+                items.emplace_back(h, ieti_solve_args(h, MODE_NEUMANN, h->gF, h->uF, h->opt.tol_inner,
+                                                      h->opt.maxit_inner, h->vst));
+            else if (j->phase == EngineJob::RECOVER)
+                items.emplace_back(h, ieti_solve_args(h, MODE_NEUMANN, h->gR, j->u, h->opt.tol_inner,
+                                                      h->opt.maxit_inner, h->vst));
+            else
+                continue;
+        } else {
+            if (!in_B(j)) continue;
+            items.emplace_back(h, ieti_solve_args(h, MODE_SCHUR, h->vS, h->wS, 0.0, 0, h->vst));
+        }
+        in.push_back(i);
+    }
+}
+
+// Half a tick as one unit: the per-job launches before a merged stage, the
+// merged launch of every job's local solves (one per kernel specialisation)
+// and the per-job launches after it.  Its launch sequence repeats for the
+// same jobs in the same phases (every steady-state outer iteration), so it is
+// captured on its second occurrence and replayed from then on as ONE graph
+// launch.  The graph owns a device copy of the merged launch's arguments and
+// slot lists (the pinned staging buffers are rewritten by other stages).
+// Stage A's duration comes from the kernels themselves: every CTA widens a
+// [start, end] globaltimer span, which the graph resets before the launch and
+// copies into the read-back area (at double offset `spanoff`) after it.
+int half_tick(ieti_engine* E, int stage, std::vector<EngineJob*>& jobs, const std::vector<size_t>& rbo,
+              size_t spanoff) {
+    std::vector<std::pair<ietidp_handle*, SolveArgs>> items;
+    std::vector<size_t> in;
+    stage_items(stage, jobs, items, in);
+    MergedPrep MP;
+    long long ntune = 0;
+    CHK(merged_prepare(E, items, MP, &ntune));   // autotuning (eager, before any capture)
+    ieti_host::g_kernel_launches += ntune;
+    const int segA = stage == 0 ? 0 : 2, segB = stage == 0 ? 1 : 3;
+    cudaStream_t st = E->st;
+    auto body = [&](const SolveArgs* da, const SlotDesc* ds) -> int {
+        CHK(segment(E, segA, jobs, rbo));
+        if (!MP.groups.empty()) {
+            if (stage == 0) {
+                CU(cudaMemsetAsync(E->d_span, 0xff, sizeof(unsigned long long), st));
+                CU(cudaMemsetAsync(E->d_span + 1, 0, sizeof(unsigned long long), st));
+            }
+            long long nl = 0;
+            CHK(merged_issue(E, MP, da, ds, stage == 0 ? E->d_span : nullptr, &nl));
+            if (stage == 0)
+                CU(cudaMemcpyAsync(E->h_rb + spanoff, E->d_span, 2 * sizeof(unsigned long long),
+                                   cudaMemcpyDeviceToHost, st));
+            ieti_host::g_kernel_launches += nl;
+            for (size_t i : in) {
+                jobs[i]->S.launches += nl;
+                if (stage == 0) jobs[i]->S.neumann_launches += 1;
+            }
+        }
+        return segment(E, segB, jobs, rbo);
+    };
+    Staging& S = stage == 0 ? E->stA : E->stB;
+    auto eager = [&]() -> int {
+        if (!MP.groups.empty()) CHK(merged_stage_copy(E, S, MP));
+        return body(S.d_args, S.d_slots);
+    };
+    if (!graphs_enabled()) return eager();
+    const auto key = segment_key(E, 10 + stage, jobs);
+    auto it = E->graphs.find(key);
+    if (it != E->graphs.end() && it->second->exec) {
+        GraphEntry& G = *it->second;
+        CU(cudaGraphLaunch(G.exec, st));
+        for (size_t i = 0; i < jobs.size(); ++i) {
+            jobs[i]->S.launches += G.dl[i];
+            jobs[i]->S.neumann_launches += G.dn[i];
+        }
+        ieti_host::g_kernel_launches += G.total;
+        return IETIDP_OK;
+    }
+    if (it == E->graphs.end() && E->seen.size() >= 4096) E->seen.clear();
+    if (it != E->graphs.end() || ++E->seen[key] < 2) return eager();
+    if (E->graphs.size() >= 256) clear_graphs(E);
+    auto G = std::make_unique<GraphEntry>();
+    if (!MP.groups.empty()) {
+        // before the capture: the graph's own argument and slot buffers
+        CU(cudaStreamSynchronize(st));
+        CU(cudaMalloc(&G->d_args, sizeof(SolveArgs) * MP.args.size()));
+        CU(cudaMalloc(&G->d_slots, sizeof(SlotDesc) * MP.slots.size()));
+        CU(cudaMemcpy(G->d_args, MP.args.data(), sizeof(SolveArgs) * MP.args.size(), cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(G->d_slots, MP.slots.data(), sizeof(SlotDesc) * MP.slots.size(), cudaMemcpyHostToDevice));
+    }
+    std::vector<long long> l0(jobs.size()), n0(jobs.size());
+    for (size_t i = 0; i < jobs.size(); ++i) {
+        l0[i] = jobs[i]->S.launches;
+        n0[i] = jobs[i]->S.neumann_launches;
+    }
+    const long long g0 = ieti_host::g_kernel_launches.load();
+    auto give_up = [&]() -> int {
+        cudaGetLastError();
+        if (G->exec) cudaGraphExecDestroy(G->exec);
+        G->exec = nullptr;
+        for (size_t i = 0; i < jobs.size(); ++i) {
+            jobs[i]->S.launches = l0[i];
+            jobs[i]->S.neumann_launches = n0[i];
+        }
+        ieti_host::g_kernel_launches = g0;
+        E->graphs[key] = std::move(G);   // not capturable: eager from now on (the buffers stay owned)
+        return eager();
+    };
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed) != cudaSuccess) return give_up();
+    int rc = body((const SolveArgs*)G->d_args, (const SlotDesc*)G->d_slots);
+    cudaError_t ce = cudaStreamEndCapture(st, &graph);
+    if (rc == IETIDP_OK && ce == cudaSuccess && graph) ce = cudaGraphInstantiate(&G->exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (rc != IETIDP_OK || ce != cudaSuccess || !G->exec) return give_up();
+    G->dl.resize(jobs.size());
+    G->dn.resize(jobs.size());
+    for (size_t i = 0; i < jobs.size(); ++i) {
+        G->dl[i] = jobs[i]->S.launches - l0[i];
+        G->dn[i] = jobs[i]->S.neumann_launches - n0[i];
+    }
+    G->total = ieti_host::g_kernel_launches.load() - g0;
+    CU(cudaGraphLaunch(G->exec, st));
+    E->graphs[key] = std::move(G);
+    return IETIDP_OK;
 }
 
 }  // namespace
@@ -735,6 +866,8 @@ int ieti_engine_tick(ieti_engine* E, std::vector<EngineJob*>& jobs) {
         rbo[i] = need;
         need += rb_stride(jobs[i]->h);
     }
+    const size_t spanoff = need;   // [start, end] of merged stage A (globaltimer ns)
+    need += 2;
     if (need > E->cap_rb) {
         CU(cudaStreamSynchronize(st));
         if (E->h_rb) cudaFreeHost(E->h_rb);
@@ -746,14 +879,13 @@ int ieti_engine_tick(ieti_engine* E, std::vector<EngineJob*>& jobs) {
     }
     bool anyA = false;
     for (EngineJob* j : jobs) anyA = anyA || in_A(j);
-    CHK(staged(E, 0, jobs, rbo));
-    CHK(merged_stage(E, 0, jobs));
-    CHK(staged(E, 1, jobs, rbo));
+    CHK(half_tick(E, 0, jobs, rbo, spanoff));
     CU(cudaStreamSynchronize(st));
     float msA = 0.f;
-    if (anyA && cudaEventElapsedTime(&msA, E->e0, E->e1) != cudaSuccess) {
-        cudaGetLastError();
-        msA = 0.f;
+    if (anyA) {
+        unsigned long long sp[2];
+        std::memcpy(sp, E->h_rb + spanoff, sizeof(sp));
+        if (sp[1] > sp[0]) msA = (float)((double)(sp[1] - sp[0]) * 1e-6);
     }
     for (EngineJob* j : jobs)
         if (j->phase == EngineJob::INIT || j->phase == EngineJob::ITER || j->phase == EngineJob::RECOVER)
@@ -817,9 +949,7 @@ int ieti_engine_tick(ieti_engine* E, std::vector<EngineJob*>& jobs) {
             finish(*j);
         }
     }
-    CHK(staged(E, 2, jobs, rbo));
-    CHK(merged_stage(E, 1, jobs));
-    CHK(staged(E, 3, jobs, rbo));
+    CHK(half_tick(E, 1, jobs, rbo, spanoff));
     for (EngineJob* j : jobs) {
         if (j->phase == EngineJob::PRECF) {
             j->it = 1;
@@ -1057,3 +1187,52 @@ extern "C" int ietidp_solve_batch_host(ietidp_handle* const* hs, int n, const do
     CHK(run_jobs(hs, n, jobs, true, f_host, u_host));
     return report(jobs, stats);
 }
+
+// V-cycles on the Neumann hierarchies of every patch of several handles in
+// one merged launch per kernel specialisation (the batched form of
+// ietidp_vcycles, timed on the engine's stream)
+extern "C" int ietidp_vcycles_batch(ietidp_handle* const* hs, int n, const double* const* b, double* const* x,
+                                    int ncycles, float* ms_out) {
+    CHK(check_batch(hs, n, x));
+    if (!b || ncycles < 0) return fail(IETIDP_E_INVALID_ARG, "bad argument");
+    for (int i = 0; i < n; ++i)
+        if (!b[i]) return fail(IETIDP_E_INVALID_ARG, "null input in batch");
+    ieti_engine* E = nullptr;
+    CHK(engine_of(hs[0], &E));
+    cudaStream_t st = E->st;
+    std::vector<cudaEvent_t> evs;
+    auto join = [&](cudaStream_t from, cudaStream_t to) -> int {
+        cudaEvent_t ev;
+        cudaError_t er = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (er == cudaSuccess) {
+            evs.push_back(ev);
+            er = cudaEventRecord(ev, from);
+        }
+        if (er == cudaSuccess) er = cudaStreamWaitEvent(to, ev, 0);
+        return er == cudaSuccess ? IETIDP_OK : fail(IETIDP_E_CUDA, std::string("stream join: ") + cudaGetErrorString(er));
+    };
+    int rc = IETIDP_OK;
+    for (int i = 0; i < n && rc == IETIDP_OK; ++i)
+        if (hs[i]->st != st) rc = join(hs[i]->st, st);
+    if (rc == IETIDP_OK) {
+        std::vector<std::pair<ietidp_handle*, SolveArgs>> items;
+        for (int i = 0; i < n; ++i) {
+            SolveArgs a = ieti_solve_args(hs[i], MODE_VCYCLE, b[i], x[i], 0.0, 0, hs[i]->vst);
+            a.ncycles = ncycles;
+            items.emplace_back(hs[i], a);
+        }
+        long long nl = 0;
+        rc = ieti_engine_merged(E, 0, items, &nl, true);
+        ieti_host::g_kernel_launches += nl;
+    }
+    if (rc == IETIDP_OK) {
+        cudaError_t er = cudaStreamSynchronize(st);
+        if (er != cudaSuccess) rc = fail(IETIDP_E_CUDA, cudaGetErrorString(er));
+        else if (ms_out) *ms_out = ieti_engine_timed_ms(E);
+    }
+    for (int i = 0; i < n && rc == IETIDP_OK; ++i)
+        if (hs[i]->st != st) rc = join(st, hs[i]->st);
+    for (auto ev : evs) cudaEventDestroy(ev);
+    return rc;
+}
+

@@ -442,6 +442,7 @@ SolveArgs ieti_solve_args(const ietidp_handle* h, int mode, const double* in, do
     a.mixed = h->opt.precision == IETIDP_PREC_MIXED;
     a.K64 = h->K64;
     a.K32 = h->K32;
+    a.K32lo = h->K32lo;
     a.KM64 = h->KM64;
     a.KM32 = h->KM32;
     a.tab = h->tab;
@@ -474,6 +475,11 @@ SolveArgs ieti_solve_args(const ietidp_handle* h, int mode, const double* in, do
     a.szW = h->szW;
     a.szHinv = h->szHinv;
     a.band = h->band;
+    static const int kflags = [] {
+        const char* e = std::getenv("IETIDP_KFLAGS");
+        return e ? std::atoi(e) : 0;
+    }();
+    a.kflags = kflags;
     if (mode == MODE_NEUMANN && h->opt.method == IETIDP_METHOD_DMG) a.mode = MODE_NEUMANN_DIRECT;
     return a;
 }
@@ -846,11 +852,14 @@ extern "C" int ietidp_setup(const iga_problem* P, const ietidp_options* opt_in, 
     bool mixed = opt.precision == IETIDP_PREC_MIXED;
     // ---- device memory -------------------------------------------------------
     CKH(h->mem.upload(&h->d_pd, h->pd, st));
-    CKH(h->mem.alloc(&h->K64, koff));
-    if (mixed) CKH(h->mem.alloc(&h->K32, koff));
+    // value pools: 16 elements of tail padding, since the local solver reads
+    // color blocks widened to 16-byte boundaries (bulk prefetches)
+    CKH(h->mem.alloc(&h->K64, koff + 16));
+    if (mixed) CKH(h->mem.alloc(&h->K32, koff + 16));
+    if (mixed) CKH(h->mem.alloc(&h->K32lo, koff + 16));
     if (h->n_floating > 0) {
-        CKH(h->mem.alloc(&h->KM64, koff));
-        if (mixed) CKH(h->mem.alloc(&h->KM32, koff));
+        CKH(h->mem.alloc(&h->KM64, koff + 16));
+        if (mixed) CKH(h->mem.alloc(&h->KM32, koff + 16));
     }
     CKH(h->mem.alloc(&h->tab, toff_tab));
     CKH(h->mem.alloc(&h->tabf, toff_tab));
@@ -957,6 +966,7 @@ extern "C" int ietidp_setup(const iga_problem* P, const ietidp_options* opt_in, 
         if (e == cudaSuccess && h->n_floating > 0)
             e = launch_regularize(h->d_pd, N, h->K64, h->tab, opt.alpha_reg, h->KM64, st);
         if (e == cudaSuccess && mixed) e = launch_to_f32(h->K64, h->K32, koff, st);
+        if (e == cudaSuccess && mixed) e = launch_lo_f32(h->K64, h->K32, h->K32lo, koff, st);
         if (e == cudaSuccess && mixed && h->n_floating > 0) e = launch_to_f32(h->KM64, h->KM32, koff, st);
         if (e == cudaSuccess) e = launch_to_f32(h->tab, h->tabf, toff_tab, st);
         if (e == cudaSuccess)

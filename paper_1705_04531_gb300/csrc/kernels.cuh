@@ -57,6 +57,8 @@ cudaError_t launch_cweights(const PatchDesc* pd, int nrows, const int* crow_ptr,
                             double* c_w, cudaStream_t st);
 
 cudaError_t launch_to_f32(const double* src, float* dst, long long n, cudaStream_t st);
+// lo = src - hi rounded to FP32 (the low part of an FP32 pair hi + lo)
+cudaError_t launch_lo_f32(const double* src, const float* hi, float* lo, long long n, cudaStream_t st);
 
 // D-MG: band of the fine K (Dirichlet and pinned dofs as identity rows) and its
 // Cholesky factor, one CTA per listed patch (direct_kernels.cu)
@@ -110,6 +112,7 @@ struct SolveArgs {
     int mixed;                 // V-cycles in FP32
     const double* K64;
     const float* K32;
+    const float* K32lo;        // K - K32 in FP32 (mixed path: K = K32 + K32lo to 48 bits)
     const double* KM64;        // K + alpha M^ (floating patches), all levels
     const float* KM32;
     const double* tab;
@@ -147,6 +150,14 @@ struct SolveArgs {
     // indexed by SlotDesc::handle; slots, nslots and smem_bytes of the launch
     // itself stay those of this struct.  nullptr: a single handle.
     const SolveArgs* batch;
+    // [start, end] of the launch in globaltimer nanoseconds (or null): thread
+    // 0 of every CTA lowers the start at entry and raises the end at exit
+    unsigned long long* tspan;
+    // kernel variant switches for measurements (IETIDP_KFLAGS, 0 = all on):
+    // 4 FP64 operator reads its input from global memory, 16 no L2 prefetch
+    // of streamed color blocks, 32 the mixed path's stiffness operator in
+    // FP64 instead of FP32 pairs
+    int kflags;
 };
 
 // generic kernel (degrees known at run time only)

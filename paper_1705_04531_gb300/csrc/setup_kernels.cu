@@ -695,6 +695,13 @@ __global__ void k_to_f32(const double* s, float* d, long long n) {
         d[i] = (float)s[i];
 }
 
+// lo = s - hi in FP32 (hi = FP32 rounding of s): hi + lo carries 48 bits of s
+__global__ void k_lo_f32(const double* s, const float* hi, float* lo, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        lo[i] = (float)(s[i] - (double)hi[i]);
+}
+
 int grid_for(long long n, int threads, int cap = 152 * 32) {
     long long b = (n + threads - 1) / threads;
     if (b < 1) b = 1;
@@ -763,6 +770,12 @@ cudaError_t launch_cweights(const PatchDesc* pd, int nrows, const int* crow_ptr,
 cudaError_t launch_to_f32(const double* s, float* d, long long n, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
     k_to_f32<<<grid_for(n, 256), 256, 0, st>>>(s, d, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lo_f32(const double* s, const float* hi, float* lo, long long n, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    k_lo_f32<<<grid_for(n, 256), 256, 0, st>>>(s, hi, lo, n);
     return cudaGetLastError();
 }
 

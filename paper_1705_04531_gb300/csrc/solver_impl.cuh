@@ -96,7 +96,8 @@ struct CTab {
 struct Plan {
     bool vec;       // x, b, r in shared memory
     bool a0;        // coarsest inverse in shared memory
-    int ls;         // matrices of levels 0..ls in shared memory (-1: none)
+    int ls;         // matrices of levels 1..ls in shared memory (0: none; the
+                    // coarsest level is solved by its dense inverse)
     size_t tab_off, vec_off, a0_off, mat_off, used;
 };
 
@@ -121,11 +122,12 @@ __host__ __device__ inline Plan make_plan(const PatchDesc& P, size_t tsize, size
     pl.a0_off = used;
     if (pl.a0) used += ab;
     pl.mat_off = used;
-    pl.ls = -1;
-    // levels 0..l are staged as one copy of their contiguous span in the
-    // value pool (including the alignment gaps between levels)
-    for (int l = 0; l < P.L - 1; ++l) {
-        size_t span = (size_t)(P.lev[l].koff + (long long)P.lev[l].n * P.lev[l].S - P.lev[0].koff) * tsize;
+    pl.ls = 0;
+    // levels 1..l are staged as one copy of their contiguous span in the
+    // value pool (including the alignment gaps between levels); the fine
+    // level too when everything fits
+    for (int l = 1; l < P.L; ++l) {
+        size_t span = (size_t)(P.lev[l].koff + (long long)P.lev[l].n * P.lev[l].S - P.lev[1].koff) * tsize;
         if (pl.mat_off + span > B) break;
         used = pl.mat_off + span;
         pl.ls = l;
@@ -143,8 +145,8 @@ inline size_t smem_need(const PatchDesc& P, size_t tsize, bool xg = false) {
     size_t b = ctab_bytes(P) + (xg ? 0 : align16(vec_elems(P) * tsize)) +
                align16((size_t)P.lev[0].n * P.lev[0].n * tsize);
     if (P.L > 1) {
-        const LevelDesc& Lt = P.lev[P.L - 2];
-        b += (size_t)(Lt.koff + (long long)Lt.n * Lt.S - P.lev[0].koff) * tsize;
+        const LevelDesc& Lt = P.lev[P.L - 1];
+        b += (size_t)(Lt.koff + (long long)Lt.n * Lt.S - P.lev[1].koff) * tsize;
     }
     return b;
 }
@@ -183,6 +185,12 @@ __device__ __forceinline__ T* shm(int elem_off) {
     return reinterpret_cast<T*>(ieti_dyn) + elem_off;
 }
 
+// bulk prefetch of [src, src + bytes) into L2 (sm_90+; nothing to wait for);
+// src and bytes 16-byte aligned
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 template <typename T, int D, int P0, int P1, int P2, bool XG>
 struct VC {
     static constexpr int W0 = 2 * P0 + 1, W1 = 2 * P1 + 1, W2 = 2 * P2 + 1;
@@ -193,7 +201,7 @@ struct VC {
     const PatchDesc* P;   // shared copy
     int mask;
     const T* Kg;          // global value pool (K or K + alpha M^)
-    int ks_off;           // staged matrices of levels 0..ls (element offset in dynamic shared memory)
+    int ks_off;           // staged matrices of levels 1..ls (element offset in dynamic shared memory)
     int ls;
     long long kbase;
     const T* tab;
@@ -209,6 +217,7 @@ struct VC {
     }
     const CTab* ct;       // [l * NC + c]
     long long* phase;     // phase timers (profiling builds)
+    int kflags;           // SolveArgs::kflags
 
     // one row of color (c0,c1,c2) at level l.  X: the row's own entry in x;
     // the neighbour at stencil offset (o0,o1,o2) lies e0(o0)+e1(o1)+e2(o2)
@@ -283,11 +292,37 @@ struct VC {
         if (WHAT == 0) __syncthreads();
     }
 
+    // A level streamed from L2/HBM: its color blocks are moved into L2 by
+    // bulk prefetches (one instruction of thread 0 per block, no registers or
+    // shared memory held) one and two color steps before the step that reads
+    // them, so the step's loads wait for L2 instead of HBM.  The copied range
+    // is the block widened to 16-byte boundaries (the value pools carry 16
+    // elements of tail padding).
+    __device__ __forceinline__ void prefetch_block(int l, int c) const {
+        if (kflags & 16) return;
+        constexpr long long A = 16 / sizeof(T);
+        const CTab t = ct[l * NC + c];
+        const long long s0 = P->lev[l].koff + (long long)t.off * S;
+        const long long len = (long long)t.k0 * t.k1 * t.k2 * S;
+        const long long a = s0 & ~(A - 1), e = (s0 + len + A - 1) & ~(A - 1);
+        bulk_prefetch_l2(Kg + a, (unsigned)((e - a) * (long long)sizeof(T)));
+    }
+
     __device__ void sweep(int l, bool forward) const {
         if (l <= ls) {
             for (int cc = 0; cc < NC; ++cc) color_pass<true, 0>(l, forward ? cc : NC - 1 - cc);
         } else {
-            for (int cc = 0; cc < NC; ++cc) color_pass<false, 0>(l, forward ? cc : NC - 1 - cc);
+            // the color after the sweep's last one is the first of the next
+            // sweep (or, after forward sweeps, of the residual)
+            auto col = [&](int k) { return forward ? k % NC : NC - 1 - k % NC; };
+            if (threadIdx.x == 0) {
+                prefetch_block(l, col(0));
+                prefetch_block(l, col(1));
+            }
+            for (int cc = 0; cc < NC; ++cc) {
+                if (threadIdx.x == 0) prefetch_block(l, col(cc + 2));
+                color_pass<false, 0>(l, col(cc));
+            }
         }
     }
 
@@ -295,7 +330,10 @@ struct VC {
         if (l <= ls) {
             for (int c = 0; c < NC; ++c) color_pass<true, 1>(l, c);
         } else {
-            for (int c = 0; c < NC; ++c) color_pass<false, 1>(l, c);
+            for (int c = 0; c < NC; ++c) {
+                if (threadIdx.x == 0) prefetch_block(l, (c + 2) % NC);
+                color_pass<false, 1>(l, c);
+            }
         }
         __syncthreads();
     }
@@ -372,6 +410,26 @@ struct VC {
             const T* w0 = tab + F.pw[0] + i0 * R0;
             const T* w1 = tab + F.pw[1] + i1 * R1;
             const T* w2 = D == 3 ? tab + F.pw[2] + i2 * R2 : nullptr;
+            // the coarse position (natural or color-major) is a sum of one
+            // term per direction: f0(q0) + f1(q1) + f2(q2)
+            int f0[R0], f1[R1], f2[R2];
+#pragma unroll
+            for (int u = 0; u < R0; ++u) {
+                const int q = a0 + u;
+                f0[u] = cnat ? q : (q % C0) * Cl.blk + q / C0 + 1;
+            }
+#pragma unroll
+            for (int u = 0; u < R1; ++u) {
+                const int q = a1 + u;
+                f1[u] = cnat ? Cl.m[0] * q : (q % C1) * C0 * Cl.blk + Cl.xk[0] * (q / C1 + 1);
+            }
+#pragma unroll
+            for (int u = 0; u < R2; ++u) {
+                const int q = a2 + u;
+                f2[u] = D != 3 ? 0
+                               : (cnat ? Cl.m[0] * Cl.m[1] * q
+                                       : (q % C2) * C0 * C1 * Cl.blk + Cl.xk[0] * Cl.xk[1] * (q / C2 + 1));
+            }
             T acc = 0;
 #pragma unroll
             for (int u2 = 0; u2 < R2; ++u2) {
@@ -383,13 +441,13 @@ struct VC {
                     const int q1 = a1 + u1;
                     if (q1 >= Cl.m[1]) continue;
                     const T ww1 = w1[u1] * ww2;
+                    const int f12 = f1[u1] + f2[u2];
                     T s = 0;
 #pragma unroll
                     for (int u0 = 0; u0 < R0; ++u0) {
                         const int q0 = a0 + u0;
                         if (q0 >= Cl.m[0]) continue;
-                        const int src = cnat ? q0 + Cl.m[0] * (q1 + Cl.m[1] * q2) : cm_pos(Cl, q0, q1, q2);
-                        s += w0[u0] * xc[src];
+                        s += w0[u0] * xc[f0[u0] + f12];
                     }
                     acc += ww1 * s;
                 }
@@ -498,16 +556,25 @@ struct VC {
 // y = K x (FP64, fine level), rows masked by `rowmask` set to 0; with `sub`,
 // y = sub + scale K x; `only` = 1 keeps interface rows (boundary rows not on
 // the Dirichlet boundary) and zeroes the others.  Rows are visited color by
-// color so that each stencil diagonal is read with unit stride.
+// color so that each stencil diagonal is read with unit stride.  With
+// xs_off >= 0, x is first copied to dynamic shared memory at that element
+// offset (doubles; a free region of at least n doubles), so that a row's
+// neighbour reads are shared-memory loads and its registers hold only the
+// streamed matrix values.
 template <int D, int P0, int P1, int P2>
 __device__ __noinline__ void spmv64(const PatchDesc& P, const double* __restrict__ K64, const double* x, double* y,
                                     int rowmask, const double* sub, double scale, int only,
-                                    long long* phase = nullptr) {
+                                    long long* phase = nullptr, int xs_off = -1) {
     constexpr int W0 = 2 * P0 + 1, W1 = 2 * P1 + 1, W2 = 2 * P2 + 1, S = W0 * W1 * W2;
     constexpr int C0 = P0 + 1, C1 = P1 + 1, C2 = P2 + 1, NC = C0 * C1 * C2;
     const LevelDesc& F = P.lev[P.L - 1];
     const int m0 = F.m[0], m1 = F.m[1], m2 = F.m[2];
     IETI_T0();
+    if (xs_off >= 0) {
+        double* xs = shm<double>(xs_off);
+        for (int i = threadIdx.x; i < F.n; i += blockDim.x) xs[i] = x[i];
+        __syncthreads();
+    }
     // all rows at once (no dependency between colors): row s of the storage
     // order belongs to the color whose range [off, off + cnt) contains it
     int kk0[C0], kk1[C1], kk2[C2];
@@ -544,9 +611,96 @@ __device__ __noinline__ void spmv64(const PatchDesc& P, const double* __restrict
                 const bool ok = (unsigned)(i0 + o0) < (unsigned)m0 && (unsigned)(i1 + o1) < (unsigned)m1 &&
                                 (unsigned)(i2 + o2) < (unsigned)m2;
                 const int xi = ok ? i + o0 + m0 * (o1 + m1 * o2) : i;
-                acc[o & 3] += __ldg(vq + (long long)o * cnt) * x[xi];
+                const double xv = xs_off >= 0 ? shm<double>(xs_off)[xi] : x[xi];
+                acc[o & 3] += __ldg(vq + (long long)o * cnt) * xv;
             }
             v = scale * ((acc[0] + acc[1]) + (acc[2] + acc[3]));
+        }
+        if (sub) v = sub[i] + v;
+        y[i] = v;
+    }
+    __syncthreads();
+    IETI_T1(49);
+}
+
+// The same operator on the mixed path, on the FP32 pipes: K = Khi + Klo
+// (Khi the FP32 rounding of K, Klo the FP32 rounding of the rest: 48
+// significant bits together) and x = xhi + xlo staged in shared memory as
+// FP32 pairs.  Each product Khi xhi is split exactly into its rounded value
+// and rounding error by an FMA, the cross terms Khi xlo + Klo xhi are formed
+// in FP32 (Klo xlo, 2^-48 relative, is dropped), and the row sum is carried as
+// an unevaluated pair (s, c) with error-free two-sums: the FP64 row sum to
+// about 2^-47 of the sum of the terms' magnitudes, for twelve FP32 operations
+// per term instead of one FP64 FMA (GB300 runs FP64 at a small fraction of
+// its FP32 rate).  xs_off: element offset (8-byte pairs) of the staging area.
+__device__ __forceinline__ void df_add(float& s, float& c, float p, float e) {
+    const float t = s + p;
+    const float bb = t - s;
+    const float err = (s - (t - bb)) + (p - bb);
+    s = t;
+    c += err + e;
+}
+
+template <int D, int P0, int P1, int P2>
+__device__ __noinline__ void spmv_df(const PatchDesc& P, const float* __restrict__ Khi, const float* __restrict__ Klo,
+                                     const double* x, double* y, int rowmask, const double* sub, double scale,
+                                     int only, long long* phase, int xs_off) {
+    constexpr int W0 = 2 * P0 + 1, W1 = 2 * P1 + 1, W2 = 2 * P2 + 1, S = W0 * W1 * W2;
+    constexpr int C0 = P0 + 1, C1 = P1 + 1, C2 = P2 + 1, NC = C0 * C1 * C2;
+    const LevelDesc& F = P.lev[P.L - 1];
+    const int m0 = F.m[0], m1 = F.m[1], m2 = F.m[2];
+    IETI_T0();
+    float2* xs = reinterpret_cast<float2*>(shm<double>(xs_off));
+    for (int i = threadIdx.x; i < F.n; i += blockDim.x) {
+        const double v = x[i];
+        const float hi = (float)v;
+        xs[i] = make_float2(hi, (float)(v - (double)hi));
+    }
+    __syncthreads();
+    int kk0[C0], kk1[C1], kk2[C2];
+#pragma unroll
+    for (int c = 0; c < C0; ++c) kk0[c] = ieti_cnt(m0, P0, c);
+#pragma unroll
+    for (int c = 0; c < C1; ++c) kk1[c] = ieti_cnt(m1, P1, c);
+#pragma unroll
+    for (int c = 0; c < C2; ++c) kk2[c] = ieti_cnt(m2, P2, c);
+    for (int s = threadIdx.x; s < F.n; s += blockDim.x) {
+        int off = 0, c = 0, cnt = 0;
+#pragma unroll 1
+        for (c = 0; c < NC; ++c) {
+            cnt = kk0[c % C0] * kk1[(c / C0) % C1] * kk2[c / (C0 * C1)];
+            if (s < off + cnt) break;
+            off += cnt;
+        }
+        const int c0 = c % C0, c1 = (c / C0) % C1, c2 = c / (C0 * C1);
+        const int k0 = kk0[c0], k1 = kk1[c1];
+        const int q = s - off;
+        const int t0 = q % k0, tr = q / k0;
+        const int t1 = tr % k1, t2 = tr / k1;
+        const int i0 = c0 + C0 * t0, i1 = c1 + C1 * t1, i2 = c2 + C2 * t2;
+        const int i = i0 + m0 * (i1 + m1 * i2);
+        bool take = !ieti_masked(rowmask, F.m, i0, i1, i2);
+        if (only == 1) take = take && ieti_on_boundary(F.m, D, i0, i1, i2) && !ieti_masked(P.dmask, F.m, i0, i1, i2);
+        double v = 0.0;
+        if (take) {
+            float sh[2] = {0.f, 0.f}, sc[2] = {0.f, 0.f};
+            const long long base = F.koff + (long long)off * S + q;
+#pragma unroll
+            for (int o = 0; o < S; ++o) {
+                const int o0 = o % W0 - P0, o1 = (o / W0) % W1 - P1, o2 = o / (W0 * W1) - P2;
+                const bool ok = (unsigned)(i0 + o0) < (unsigned)m0 && (unsigned)(i1 + o1) < (unsigned)m1 &&
+                                (unsigned)(i2 + o2) < (unsigned)m2;
+                const int xi = ok ? i + o0 + m0 * (o1 + m1 * o2) : i;
+                const float2 xv = xs[xi];
+                const float ah = __ldg(Khi + base + (long long)o * cnt);
+                const float al = __ldg(Klo + base + (long long)o * cnt);
+                const float pr = ah * xv.x;
+                const float pe = fmaf(ah, xv.x, -pr);
+                const float cr = fmaf(ah, xv.y, al * xv.x);
+                df_add(sh[o & 1], sc[o & 1], pr, pe + cr);
+            }
+            df_add(sh[0], sc[0], sh[1], sc[1]);
+            v = scale * ((double)sh[0] + (double)sc[0]);
         }
         if (sub) v = sub[i] + v;
         y[i] = v;
@@ -629,6 +783,7 @@ __device__ inline void apply_C(const SolveArgs& a, const PatchDesc& P, const dou
 
 template <typename T, int D, int P0, int P1, int P2, bool XG>
 __global__ void __launch_bounds__(512) k_solve_t(SolveArgs a0) {
+    const IetiLaunchSpan span_(a0.tspan);
     __shared__ Red red;
     __shared__ double coef[kMaxRows];
     __shared__ PatchDesc sP;
@@ -666,6 +821,9 @@ __global__ void __launch_bounds__(512) k_solve_t(SolveArgs a0) {
     const T* A0g = (a.mixed ? (const T*)(const void*)a.A0inv32 : (const T*)(const void*)a.A0inv64) + P.a0off[kind];
 
     const Plan pl = make_plan(P, sizeof(T), a.smem_bytes, !XG);
+    // the V-cycle vectors are dead between V-cycles (at least 12 n bytes in
+    // the mixed path): the FP64 operator stages its input vector there
+    const int xs_off = (!XG && pl.vec && !(a.kflags & 4)) ? (int)(pl.vec_off / sizeof(double)) : -1;
     const bool reg = kind == 0 && P.floating;
     const T* Kv = a.mixed ? (const T*)(const void*)(reg ? a.KM32 : a.K32)
                           : (const T*)(const void*)(reg ? a.KM64 : a.K64);
@@ -681,7 +839,8 @@ __global__ void __launch_bounds__(512) k_solve_t(SolveArgs a0) {
         vc.gvec = (T*)a.lv + sd.lv;
         vc.b_off = vc.x_off + P.nlx;
         vc.r_off = vc.b_off + P.nlb;
-        vc.kbase = P.lev[0].koff;
+        vc.kbase = P.L > 1 ? P.lev[1].koff : 0;
+        vc.kflags = a.kflags;
         vc.ls = pl.ls;
         vc.ks_off = (int)(pl.mat_off / sizeof(T));
         vc.a0_off = pl.a0 ? (int)(pl.a0_off / sizeof(T)) : -1;
@@ -696,23 +855,32 @@ __global__ void __launch_bounds__(512) k_solve_t(SolveArgs a0) {
         const int nn = P.lev[0].n * P.lev[0].n;
         for (int t = threadIdx.x; t < nn; t += blockDim.x) dst[t] = A0g[t];
     }
-    if (pl.ls >= 0) {
+    if (pl.ls >= 1) {
         T* dst = (T*)(dyn + pl.mat_off);
-        const long long cnt = P.lev[pl.ls].koff + (long long)P.lev[pl.ls].n * P.lev[pl.ls].S - P.lev[0].koff;
-        const T* src = Kv + P.lev[0].koff;
+        const long long cnt = P.lev[pl.ls].koff + (long long)P.lev[pl.ls].n * P.lev[pl.ls].S - P.lev[1].koff;
+        const T* src = Kv + P.lev[1].koff;
         for (long long t = threadIdx.x; t < cnt; t += blockDim.x) dst[t] = src[t];
     }
     __syncthreads();
     long long vcount = 0;
 
+    // the stiffness operator of the solve phase (CG, Schur complement,
+    // V-cycle residuals): on the mixed path in FP32-pair arithmetic, else FP64
+    const bool df = sizeof(T) == 4 && xs_off >= 0 && a.K32lo && !(a.kflags & 32);
+    auto opK = [&](const double* in, double* out, int rmask, const double* sb, double sc, int only, long long* ph) {
+        if (df)
+            spmv_df<D, P0, P1, P2>(P, a.K32, a.K32lo, in, out, rmask, sb, sc, only, ph, xs_off);
+        else
+            spmv64<D, P0, P1, P2>(P, a.K64, in, out, rmask, sb, sc, only, ph, xs_off);
+    };
     if (a.mode == MODE_SCHUR) {
         const double* v = a.in + P.toff;
-        spmv64<D, P0, P1, P2>(P, a.K64, v, r, allsides, nullptr, -1.0, 0);
+        opK(v, r, allsides, nullptr, -1.0, 0, nullptr);
         for (int c = 0; c < a.ncycles; ++c) {
             if (c == 0) {
                 vcycle_apply(vc, r, x, a.nu1, a.nu2);
             } else {
-                spmv64<D, P0, P1, P2>(P, a.K64, x, q, allsides, r, -1.0, 0);
+                opK(x, q, allsides, r, -1.0, 0, nullptr);
                 vcycle_apply(vc, q, z, a.nu1, a.nu2);
                 for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] += z[i];
                 __syncthreads();
@@ -721,7 +889,7 @@ __global__ void __launch_bounds__(512) k_solve_t(SolveArgs a0) {
         }
         for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = v[i] + x[i];
         __syncthreads();
-        spmv64<D, P0, P1, P2>(P, a.K64, p, a.out + P.toff, 0, nullptr, 1.0, 1);
+        opK(p, a.out + P.toff, 0, nullptr, 1.0, 1, nullptr);
         if (threadIdx.x == 0 && a.vstats) {
             atomicAdd((unsigned long long*)&a.vstats[0], (unsigned long long)vcount);
             atomicAdd((unsigned long long*)&a.vstats[1], (unsigned long long)(vcount * n));
@@ -734,7 +902,7 @@ __global__ void __launch_bounds__(512) k_solve_t(SolveArgs a0) {
         double* xx = a.out + P.toff;
         const int rmask = kind == 0 ? P.dmask : allsides;
         for (int c = 0; c < a.ncycles; ++c) {
-            spmv64<D, P0, P1, P2>(P, a.K64, xx, r, rmask, bb, -1.0, 0, a.phase);
+            opK(xx, r, rmask, bb, -1.0, 0, a.phase);
             for (int i = threadIdx.x; i < n; i += blockDim.x) {
                 const int i0 = i % F.m[0], ir = i / F.m[0];
                 const int i1 = ir % F.m[1], i2 = ir / F.m[1];
@@ -777,12 +945,12 @@ __global__ void __launch_bounds__(512) k_solve_t(SolveArgs a0) {
             __syncthreads();
             double rho = 0.0;
             for (int it = 0; it < a.maxit; ++it) {
-                spmv64<D, P0, P1, P2>(P, A64, x, r, P.dmask, nullptr, 1.0, 0);
+                spmv64<D, P0, P1, P2>(P, A64, x, r, P.dmask, nullptr, 1.0, 0, nullptr, xs_off);
                 vcycle_apply(vc, r, z, a.nu1, a.nu2);
                 ++vcount;
                 for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = x[i] - z[i];
                 __syncthreads();
-                spmv64<D, P0, P1, P2>(P, A64, p, q, P.dmask, nullptr, 1.0, 0);
+                spmv64<D, P0, P1, P2>(P, A64, p, q, P.dmask, nullptr, 1.0, 0, nullptr, xs_off);
                 double s3[3] = {0.0, 0.0, 0.0};
                 for (int i = threadIdx.x; i < n; i += blockDim.x) {
                     s3[0] += x[i] * r[i];
@@ -820,7 +988,7 @@ __global__ void __launch_bounds__(512) k_solve_t(SolveArgs a0) {
                 if (c == 0) {
                     vcycle_apply(vc, r, x, a.nu1, a.nu2);
                 } else {
-                    spmv64<D, P0, P1, P2>(P, A64, x, q, P.dmask, r, -1.0, 0);
+                    spmv64<D, P0, P1, P2>(P, A64, x, q, P.dmask, r, -1.0, 0, nullptr, xs_off);
                     vcycle_apply(vc, q, z, a.nu1, a.nu2);
                     for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] += z[i];
                     __syncthreads();
@@ -850,7 +1018,7 @@ __global__ void __launch_bounds__(512) k_solve_t(SolveArgs a0) {
             ++vcount;
         };
         auto spk = [&](const double* in, double* out) {
-            spmv64<D, P0, P1, P2>(P, a.K64, in, out, P.dmask, nullptr, 1.0, 0);
+            spmv64<D, P0, P1, P2>(P, a.K64, in, out, P.dmask, nullptr, 1.0, 0, nullptr, xs_off);
         };
         double* base = a.cg + sd.cg;
         int it = 0;
@@ -884,7 +1052,7 @@ __global__ void __launch_bounds__(512) k_solve_t(SolveArgs a0) {
             if (IETI_OK(a.c_idx[e], n, 14)) z[a.c_idx[e]] = 1.0;
         __syncthreads();
         for (int i = threadIdx.x; i < n; i += blockDim.x) phicol[i] = z[i];
-        spmv64<D, P0, P1, P2>(P, a.K64, z, r, P.dmask, nullptr, -1.0, 0);
+        spmv64<D, P0, P1, P2>(P, a.K64, z, r, P.dmask, nullptr, -1.0, 0, nullptr, xs_off);
         project_kerC(a, P, r, coef);
     } else {
         const double* g = a.in + P.toff;
@@ -944,7 +1112,10 @@ __global__ void __launch_bounds__(512) k_solve_t(SolveArgs a0) {
         }
         for (it = 1; it <= a.maxit; ++it) {
             double s[1] = {0.0};
-            spmv64<D, P0, P1, P2>(P, a.K64, p, q, P.dmask, nullptr, 1.0, 0, a.phase);
+            if (basis)
+                spmv64<D, P0, P1, P2>(P, a.K64, p, q, P.dmask, nullptr, 1.0, 0, a.phase, xs_off);
+            else
+                opK(p, q, P.dmask, nullptr, 1.0, 0, a.phase);
             if (basis) project_kerC(a, P, q, coef);
             for (int i = threadIdx.x; i < n; i += blockDim.x) s[0] += p[i] * q[i];
             cta_sum<1>(s, red);

@@ -380,6 +380,7 @@ __device__ void apply_C(const SolveArgs& a, const PatchDesc& P, const double* v,
 
 template <typename T>
 __global__ void __launch_bounds__(512) k_solve(SolveArgs a0) {
+    const IetiLaunchSpan span_(a0.tspan);
     __shared__ Red red;
     __shared__ double coef[kMaxRows];
     __shared__ SolveArgs sa;

@@ -106,6 +106,8 @@ _SIGS = {
     "ietidp_kernel_launches": (C.c_longlong, []),
     "ietidp_vcycles": (C.c_int, [_vp, _vp, _vp, C.c_int]),
     "ietidp_vcycles_hierarchy": (C.c_int, [_vp, C.c_int, _vp, _vp, C.c_int]),
+    "ietidp_vcycles_batch": (C.c_int, [C.POINTER(_vp), C.c_int, C.POINTER(_vp), C.POINTER(_vp), C.c_int,
+                                       C.POINTER(C.c_float)]),
     "ietidp_vcycles_noalloc": (C.c_int, [_vp, _vp, _vp, C.c_int]),
     "ietidp_apply_K": (C.c_int, [_vp, _vp, _vp]),
     "ietidp_apply_F": (C.c_int, [_vp, _vp, _vp]),
@@ -383,6 +385,18 @@ class Solver:
 
     def vcycles(self, b, x, ncycles):
         _check(_lib.ietidp_vcycles(self.h, _ptr(b), _ptr(x), int(ncycles)))
+
+    @staticmethod
+    def vcycles_batch(solvers, bs, xs, ncycles):
+        """V-cycles over the Neumann hierarchies of every patch of several
+        solvers in merged launches; returns their duration in ms."""
+        n = len(solvers)
+        hv = (_vp * n)(*[s.h for s in solvers])
+        bv = (_vp * n)(*[C.c_void_p(t.data_ptr()) for t in bs])
+        xv = (_vp * n)(*[C.c_void_p(t.data_ptr()) for t in xs])
+        ms = C.c_float(0.0)
+        _check(_lib.ietidp_vcycles_batch(hv, n, bv, xv, int(ncycles), C.byref(ms)))
+        return float(ms.value)
 
     def vcycles_hierarchy(self, hierarchy, b, x, ncycles):
         """V-cycles on the Neumann (0) or Dirichlet (1) hierarchy of every patch."""
