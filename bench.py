@@ -62,8 +62,8 @@ def parse():
                          "serve: Poisson-arrival request stream through the continuous-batching server; "
                          "profile: one batched solve of --batch copies inside a profiler range "
                          "(cudaProfilerStart/Stop), after a warm-up solve")
-    ap.add_argument("--rate", type=float, default=100.0, help="serve: arrivals per second")
-    ap.add_argument("--nreq", type=int, default=64, help="serve: requests in the stream")
+    ap.add_argument("--rate", type=float, default=None, help="serve: arrivals per second (one rate)")
+    ap.add_argument("--nreq", type=int, default=512, help="serve: requests in the stream")
     ap.add_argument("--concurrency", type=int, default=8, help="serve: worker streams")
     ap.add_argument("--budget-gb", type=float, default=64.0, help="serve: device memory budget")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
@@ -71,7 +71,12 @@ def parse():
                     help="serve / profile: outer method (MG-MG, MG-MG-S, D-MG)")
     ap.add_argument("--batch", type=int, default=8,
                     help="independent copies of the workload solved in lockstep per step")
-    return ap.parse_args()
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the other workloads (2x2 square, uneven 8x8, 2x2x2 cube) and the serving stream")
+    ap.add_argument("--serve-rates", default="100,1000", help="default run: arrival rates of the serving stream")
+    a = ap.parse_args()
+    a.rate_given = a.rate is not None
+    return a
 
 
 def workload(name):
@@ -176,9 +181,10 @@ class Clocks:
 
 
 # ---------------------------------------------------------------------------
-def oracle_run(dom, budget_s=30.0):
-    """The oracle (D-D variant: sparse LU local solves) timed on the host on
-    complete solves of the same workload (setup excluded)."""
+def oracle_run(dom, budget_s=60.0, min_solves=20):
+    """The oracle (D-D variant: sparse LU local solves) timed on one host core
+    on complete solves of the same workload (setup excluded): `min_solves`
+    solves or `budget_s` seconds, whichever comes first."""
     from oracle import ietidp as O
     t0 = time.perf_counter()
     s = O.IETIDP(dom, O.Options(mode="direct"))
@@ -190,9 +196,47 @@ def oracle_run(dom, budget_s=30.0):
         t = time.perf_counter()
         u = s.solve()
         times.append(time.perf_counter() - t)
-        if sum(times) > budget_s or len(times) >= 3:
+        if sum(times) > budget_s or len(times) >= min_solves:
             break
     return {"u": u, "times": times, "setup_s": t_setup, "outer_it": s.stats.outer_it}
+
+
+def _oracle_worker(job):
+    """Child process of the multi-core oracle legs: set-up, then `n` timed
+    solves in the given mode (one core per process)."""
+    mode, n, name = job
+    from oracle import ietidp as O
+    s = O.IETIDP(workload(name), O.Options(mode=mode))
+    times = []
+    for _ in range(n):
+        s.stats = O.Stats()
+        t = time.perf_counter()
+        s.solve()
+        times.append(time.perf_counter() - t)
+    return times
+
+
+def oracle_legs(name):
+    """The oracle beside its D-D 1-core figure: the MG-MG mode (multigrid
+    local solves) on one core, one complete solve; the D-D mode on every host
+    core, one process per core solving its own copy (spawned processes, so no
+    CUDA state is inherited)."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    ncores = os.cpu_count() or 1
+    out = {}
+    with ctx.Pool(1) as pool:
+        t = pool.map(_oracle_worker, [("mg", 1, name)])[0]
+    out["mg_1core"] = {"value": len(t) / sum(t), "unit": UNIT, "cores": 1, "solves": len(t),
+                       "sample": f"{len(t)} complete MG-MG solve of {name} (multigrid local solves), setup excluded"}
+    with ctx.Pool(ncores) as pool:
+        res = pool.map(_oracle_worker, [("direct", 2, name)] * ncores)
+    wall = max(sum(r) for r in res)
+    nsol = sum(len(r) for r in res)
+    out["dd_all_cores"] = {"value": nsol / wall, "unit": UNIT, "cores": ncores, "solves": nsol,
+                           "sample": f"{ncores} processes x 2 complete D-D solves of {name}, setup excluded; "
+                                     f"time = the slowest process's solve time"}
+    return out
 
 
 def relerr(got, ref):
@@ -308,6 +352,145 @@ def time_batch(api, torch, dom, prec, args, flush, stream, method="dual"):
             "launches": launches, "setup_ms": setup_ms}
 
 
+def time_copies(api, torch, dom, prec, B, steps, warmup, flush, stream, method="dual"):
+    """B independent copies of `dom` solved in lockstep (ietidp_solve_batch);
+    CUDA events on the launching stream around each of `steps` timed steps."""
+    t0 = time.perf_counter()
+    probs = [api.Problem(dom) for _ in range(B)]
+    sols = [api.Solver(p, precision=prec, method=method) for p in probs]
+    torch.cuda.synchronize()
+    setup_ms = 1e3 * (time.perf_counter() - t0) / B
+    fs = [p.load() for p in probs]
+    us = [torch.empty(s.n_torn, dtype=torch.float64, device="cuda") for s in sols]
+    for _ in range(warmup):
+        api.Solver.solve_batch(sols, fs, us)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    stats = []
+    n0 = api.kernel_launches()
+    for k in range(steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        _, st = api.Solver.solve_batch(sols, fs, us)
+        ev[k][1].record(stream)
+        stats.append(st)
+    torch.cuda.synchronize()
+    launches = api.kernel_launches() - n0
+    ms = [a.elapsed_time(b) for a, b in ev]
+    return {"sols": sols, "probs": probs, "fs": fs, "us": us, "ms": ms, "stats": stats,
+            "launches": launches, "setup_ms": setup_ms}
+
+
+def batched_vcycles(api, torch, bt, reps=10):
+    """One V-cycle over the Neumann hierarchies of every patch of every copy
+    in merged launches (ietidp_vcycles_batch): median duration of `reps`."""
+    xs = [torch.zeros_like(f) for f in bt["fs"]]
+    for _ in range(2):
+        api.Solver.vcycles_batch(bt["sols"], bt["fs"], xs, 1)
+    return float(np.median([api.Solver.vcycles_batch(bt["sols"], bt["fs"], xs, 1) for _ in range(reps)]))
+
+
+def patch_avg_bytes(dom, sv):
+    """Algorithmic bytes of one CG iteration averaged over the patches."""
+    return float(np.mean([bytes_per_iteration(dom.patch_nelem(k), dom.patch_degree(k), sv)
+                          for k in range(dom.npatch)]))
+
+
+def extra_workload(api, torch, name, B, steps, warmup, flush, stream, peak):
+    """Solves/s, latency, iterations, accuracy against the FP64 path, batched
+    V-cycle DoF/s and the merged Neumann launches against the HBM roofline for
+    one more workload (mixed path, B copies per step; one copy for latency)."""
+    dom = workload(name)
+    bt = time_copies(api, torch, dom, "mixed", B, steps, warmup, flush, stream)
+    sts = bt["stats"]
+    ms = bt["ms"]
+    s0, f0, u0 = bt["sols"][0], bt["fs"][0], bt["us"][0]
+    lat = []
+    for k in range(steps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        e0.record(stream)
+        s0.solve(f0, u0)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if k > 0:
+            lat.append(e0.elapsed_time(e1))
+    ref_sol = api.Solver(bt["probs"][0], precision="fp64")
+    uref, st64 = ref_sol.solve(f0)
+    torch.cuda.synchronize()
+    uref_p = ref_sol.split(uref)
+    err = max(relerr(bt["sols"][i].split(bt["us"][i]), uref_p) for i in range(B))
+    ref_sol.close()
+    vc_ms = batched_vcycles(api, torch, bt)
+    nfine = sum(dom.patch_ndof(k) for k in range(dom.npatch)) * B
+    bpi = patch_avg_bytes(dom, 4)
+    iters = sum(s["inner_its"] for st in sts for s in st)
+    nl = sum(st[0]["neumann_launches"] for st in sts)
+    kms = sum(st[0]["neumann_ms"] for st in sts)
+    alg = iters * bpi / max(1, nl)
+    lms = kms / max(1, nl)
+    ach = alg / (lms / 1e3) / 1e9
+    out = {"value": B * len(ms) / (sum(ms) / 1e3), "unit": "solves/s", "batch": B,
+           "ms_per_step": sum(ms) / len(ms),
+           "p50_ms": float(np.percentile(ms, 50)), "p99_ms": float(np.percentile(ms, 99)),
+           "single_p50_ms": float(np.percentile(lat, 50)), "single_p99_ms": float(np.percentile(lat, 99)),
+           "outer_it": sts[-1][0]["outer_it"], "inner_it_avg": sts[-1][0]["inner_it_avg"],
+           "outer_it_fp64": st64["outer_it"], "rel_err_vs_fp64_gpu": err,
+           "setup_ms": bt["setup_ms"],
+           "vcycle_dofs_per_s_batched": nfine / (vc_ms / 1e3), "vcycle_ms_batched": vc_ms,
+           "roofline": {"bound": "hbm", "kernel": "merged Neumann PCG + V-cycle launches (all specialisations)",
+                        "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                        "alg_bytes_per_launch": alg, "launch_ms": lms, "launches": nl,
+                        "bytes_per_cg_iteration": "patch average (CG iterations taken equal across patches)"},
+           "patches": dom.npatch, "torn_dofs": int(nfine // B)}
+    close_batch(bt)
+    return out
+
+
+def serve_stream(api, torch, nreq, rate, seed, concurrency, budget_gb, precision="mixed", method="dual"):
+    """Poisson-arrival request stream through the continuous-batching server:
+    solves/s, p50/p99 latency (arrival to result) and the peak of the
+    admitted requests' estimated device memory (sampled every 5 ms)."""
+    reqs = W.serving_stream(nreq=nreq, rate=rate, seed=seed)
+    srv = api.Server(int(budget_gb * (1 << 30)), max_concurrent=concurrency, precision=precision, method=method)
+    srv.wait(srv.submit(W.serving_stream(nreq=1, rate=1.0, seed=99, ms=(2,), ns=(16,))[0].domain))
+    torch.cuda.synchronize()
+    peak = [0]
+    stop = threading.Event()
+
+    def sample():
+        while not stop.is_set():
+            try:
+                peak[0] = max(peak[0], srv.status()["in_flight_bytes"])
+            except Exception:
+                pass
+            time.sleep(0.005)
+
+    th = threading.Thread(target=sample, daemon=True)
+    th.start()
+    t0 = time.perf_counter()
+    tickets = []
+    for r in reqs:
+        dt = t0 + r.arrival - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        tickets.append(srv.submit(r.domain))
+    lat, runs, its = [], [], []
+    for t in tickets:
+        state, u, st, tm = srv.wait(t)
+        lat.append(tm["latency_s"])
+        runs.append(tm["run_s"])
+        its.append(st["outer_it"])
+    t1 = time.perf_counter()
+    stop.set()
+    th.join(timeout=1.0)
+    srv.close()
+    return {"rate_per_s": rate, "requests": nreq, "seed": seed, "value": nreq / (t1 - t0), "unit": "solves/s",
+            "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+            "run_p50_ms": 1e3 * float(np.percentile(runs, 50)), "outer_it_mean": float(np.mean(its)),
+            "admitted_bytes_peak": int(peak[0]), "wall_s": t1 - t0}
+
+
 def close_batch(bt):
     for s in bt["sols"]:
         s.close()
@@ -352,47 +535,22 @@ def run_vcycle_probe(args):
 
 
 def run_serve(args):
-    """Serving stream: m x m unit-square patch grids (m in {2,4,6,8}), p in
+    """Serving stream (m x m unit-square patch grids, m in {2,4,6,8}, p in
     {2,3}, 16..128 elements per patch direction, f = 8 random sine modes,
-    Poisson arrivals at --rate; continuous batching with an HBM budget."""
+    Poisson arrivals) through the continuous-batching server, one line per
+    rate of --serve-rates (or --rate when given)."""
     import torch
     from paper_1705_04531_gb300 import build
     build.build()
     from paper_1705_04531_gb300 import ietidp as api
-    stream = W.serving_stream(nreq=args.nreq, rate=args.rate, seed=0)
-    srv = api.Server(int(args.budget_gb * (1 << 30)), max_concurrent=args.concurrency,
-                     precision=args.precision, method=args.method)
-    # warm-up: one small request (module load, kernel attributes)
-    srv.wait(srv.submit(W.serving_stream(nreq=1, rate=1.0, seed=99, ms=(2,), ns=(16,))[0].domain))
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    tickets = []
-    for r in stream:
-        dt = t0 + r.arrival - time.perf_counter()
-        if dt > 0:
-            time.sleep(dt)
-        tickets.append(srv.submit(r.domain))
-    lat, runs, its = [], [], []
-    for t in tickets:
-        state, u, st, tm = srv.wait(t)
-        lat.append(tm["latency_s"])
-        runs.append(tm["run_s"])
-        its.append(st["outer_it"])
-    t1 = time.perf_counter()
-    srv.close()
-    dofs = sum(sum(r.domain.patch_ndof(k) for k in range(r.domain.npatch)) for r in stream)
-    line = {"mode": "serve", "metric": "IETI-DP solves/sec (serving stream, each request assembled, set up and solved)",
-            "value": len(stream) / (t1 - t0), "unit": "solves/s", "n_gpus": 1,
-            "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
-            "run_p50_ms": 1e3 * float(np.percentile(runs, 50)),
-            "config": {"workload": "serving stream (m in {2,4,6,8}, p in {2,3}, n in {16,32,64,128})",
-                       "requests": len(stream), "rate_per_s": args.rate, "concurrency": args.concurrency,
-                       "budget_gb": args.budget_gb, "precision": args.precision, "method": args.method,
-                       "torn_dofs_total": dofs},
-            "outer_it_mean": float(np.mean(its)), "wall_s": t1 - t0}
-    print(json.dumps(line), flush=True)
-
-
+    rates = [args.rate] if args.rate_given else [float(v) for v in args.serve_rates.split(",") if v]
+    for r in rates:
+        res = serve_stream(api, torch, args.nreq, r, 0, args.concurrency, args.budget_gb, args.precision, args.method)
+        res.update({"mode": "serve", "metric": "IETI-DP solves/sec (serving stream, each request assembled, "
+                                              "set up and solved)", "n_gpus": 1,
+                    "config": {"concurrency": args.concurrency, "budget_gb": args.budget_gb,
+                               "precision": args.precision, "method": args.method}})
+        print(json.dumps(res), flush=True)
 
 
 def run_profile(args):
@@ -520,6 +678,8 @@ def main():
     e2e_val = world * args.batch * len(e2e_t) / max_over_ranks(sum(e2e_t), dist, "cuda")
     achieved, alg_bytes_per_launch, launch_ms, nlaunch = roofline(bt, dom, 4)
     sts = bt["stats"]
+    bvc_ms = batched_vcycles(api, torch, bt)
+    bvc_dofs = nfine * args.batch / (bvc_ms / 1e3)
     close_batch(bt)
 
     # MG-MG-S (BPCG on the saddle-point system, 3 V-cycles in the K~
@@ -545,6 +705,16 @@ def main():
            "rel_err_vs_fp64_dual": dmg_err,
            "note": "D-MG: direct banded-Cholesky local Neumann solves, multigrid Dirichlet problems, same batch"}
     close_batch(bd)
+    peak, peak_kind = peaks()
+    # the other workloads of the benchmark family and the serving stream
+    # (single process only: with several ranks the line reports the headline)
+    extra, serve = {}, []
+    if world == 1 and not args.no_extra:
+        xs_ = min(args.steps, 5)
+        for nm, B in (("square2x2_p2_n16", 8), ("uneven8x8_s0", 2), ("cube2x2x2_p2_n32", 4)):
+            extra[nm] = extra_workload(api, torch, nm, B, xs_, 2, flush, stream, peak)
+        for r_ in [float(v) for v in args.serve_rates.split(",") if v]:
+            serve.append(serve_stream(api, torch, args.nreq, r_, 0, args.concurrency, args.budget_gb))
     tune = api.autotune_table()
 
     if rank != 0:
@@ -553,7 +723,6 @@ def main():
             dist.destroy_process_group()
         return
 
-    peak, peak_kind = peaks()
     traffic = None
     tp = os.path.join(ROOT, "profiles", "traffic.txt")
     if os.path.exists(tp):
@@ -596,6 +765,7 @@ def main():
         "mg_mg_s": saddle,
         "d_mg": dmg,
         "vcycle_dofs_per_s": vcycle_dofs_s, "vcycle_ms": vc_ms,
+        "vcycle_dofs_per_s_batched": bvc_dofs, "vcycle_ms_batched": bvc_ms,
         "roofline": {"bound": "hbm", "kernel": "k_solve_t<float,2,3,3,0> (merged Neumann PCG + V-cycles)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_kind": peak_kind, "traffic": traffic,
@@ -606,6 +776,12 @@ def main():
         "gpu_launches": int(bt["launches"]),
         "clocks": clk.summary(),
     }
+    if extra:
+        line["workloads"] = extra
+    if serve:
+        line["serve"] = {"stream": f"{args.nreq} requests, m x m unit-square patches, m in {{2,4,6,8}}, p in {{2,3}}, "
+                                   "n in {16,32,64,128}, f = 8 random sine modes, Poisson arrivals",
+                         "concurrency": args.concurrency, "budget_gb": args.budget_gb, "rates": serve}
     if not args.no_cpu_baseline:
         orc = oracle_run(dom)
         ref = orc["u"]
@@ -616,7 +792,9 @@ def main():
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": f"{len(orc['times'])} complete D-D solves of {args.workload} "
                                           f"(sparse LU local solves), setup excluded",
-                                "outer_it": orc["outer_it"]}
+                                "outer_it": orc["outer_it"], "p50_ms": 1e3 * float(np.percentile(orc["times"], 50)),
+                                "p99_ms": 1e3 * float(np.percentile(orc["times"], 99))}
+        line["cpu_baseline"].update(oracle_legs(args.workload))
     print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
