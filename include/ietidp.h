@@ -88,7 +88,7 @@ extern "C" {
                                  coarse Cholesky FP64                        */
 
 typedef struct {
-    int    degree[3];   /* spline degree p_r >= 1 per direction (d entries)   */
+    int    degree[3];   /* spline degree 1 <= p_r <= 7 per direction (d entries) */
     int    nelem[3];    /* uniform elements n_r >= 1 per direction            */
     int    geo_kind;    /* IGA_GEO_*                                          */
     double lo[3];       /* box corner (physical for BOX, parameter for ANNULUS)*/
@@ -146,6 +146,19 @@ typedef struct ietidp_handle ietidp_handle;
 #define IETIDP_BASIS_SZ        0
 #define IETIDP_BASIS_NULLSPACE 1
 
+/* Multigrid of the local problems (Sec. 4).  STANDARD: nested grids with the
+ * patch degree on every level, knot-insertion transfers, multicolor
+ * Gauss-Seidel.  HIGHORDER (the paper's choice for p = 4 and 7): degree 1 on
+ * every level but the finest (the degree-1 space on half the elements and
+ * its dyadic coarsenings), L2-projection transfers between the finest level
+ * and the first degree-1 level, and on the finest level a subspace-corrected
+ * mass smoother (after Hofreither and Takacs, SIAM J. Numer. Anal. 55, 2017)
+ * with a rank-one approximation of the geometry, applied by fast
+ * diagonalization; Gauss-Seidel on the degree-1 levels.  HIGHORDER needs an
+ * even element count per direction; 3D patches must be boxes. */
+#define IETIDP_MG_STANDARD  0
+#define IETIDP_MG_HIGHORDER 1
+
 typedef struct {
     unsigned primal;          /* IETIDP_PRIMAL_* bitmask                       */
     int    precision;         /* IETIDP_PREC_*                                 */
@@ -163,6 +176,7 @@ typedef struct {
     int    saddle_vcycles;    /* MG-MG-S: V-cycles in the K~ preconditioner (3) */
     double saddle_theta;      /* MG-MG-S: block scaling theta (0.9)            */
     int    basis_method;      /* IETIDP_BASIS_* (Schoeberl-Zulehner CG)        */
+    int    mg_kind;           /* IETIDP_MG_* (standard h-multigrid)            */
 } ietidp_options;
 
 typedef struct {

@@ -16,7 +16,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libietidp.so")
 SOURCES = ["setup_kernels.cu", "solver_kernels.cu", "dual_kernels.cu", "ietidp_host.cu", "ietidp_engine.cu",
            "ietidp_saddle.cu", "saddle_kernels.cu", "direct_kernels.cu",
-           "ietidp_server.cu",
+           "ietidp_server.cu", "highorder_setup.cu",
            "solver_dispatch.cu"] + sorted(f for f in os.listdir(SRC) if f.startswith("solver_t_"))
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]

@@ -21,7 +21,7 @@
 
 #define IETI_MAXD 3
 #define IETI_MAXLEV 12
-#define IETI_MAXP 6
+#define IETI_MAXP 8
 
 struct LevelDesc {
     int m[3];          // functions per direction (1 for unused directions)

@@ -76,6 +76,7 @@ struct DevMem {
 struct iga_problem {
     int dim = 0, npatch = 0;
     std::vector<iga_patch_desc> patches;
+    std::vector<iga_interface_desc> interfaces;   // as given (companion problems of the high-order multigrid)
     std::vector<int> m;          // npatch*3 functions per direction
     std::vector<int> dmask;
     std::vector<long long> toff; // npatch+1
@@ -126,6 +127,15 @@ struct ietidp_handle {
     int* itab = nullptr;
     double* A0inv64 = nullptr;
     float* A0inv32 = nullptr;
+    // high-order multigrid: per-patch descriptors and operator pools, and the
+    // companion degree-1 problem whose standard hierarchies sit below the
+    // finest level (set up as a handle of its own, destroyed with this one)
+    std::vector<HoDesc> ho;
+    HoDesc* d_ho = nullptr;
+    double* ho64 = nullptr;
+    float* ho32 = nullptr;
+    iga_problem* ho_prob = nullptr;
+    ietidp_handle* ho_sub = nullptr;
     // constraints
     int nrows = 0, npi = 0;
     int *crow_ptr = nullptr, *c_idx = nullptr, *crow_patch = nullptr, *crow_local = nullptr,
@@ -177,6 +187,10 @@ struct ietidp_handle {
     struct ieti_engine* engine = nullptr;   // solve engine on this handle's stream (created on first solve)
     struct ieti_saddle_bufs* saddle = nullptr;   // MG-MG-S vectors (created on first saddle solve)
 };
+
+// high-order multigrid operators of every patch (highorder_setup.cu)
+int ieti_ho_build(const iga_problem* Pb, const std::vector<PatchDesc>& pd, double alpha, std::vector<HoDesc>& desc,
+                  std::vector<double>& pool);
 
 // release the host part of the MG-MG-S buffers (device memory is the handle's)
 void ieti_saddle_free(ietidp_handle* h);

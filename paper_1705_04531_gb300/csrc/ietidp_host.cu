@@ -85,6 +85,7 @@ extern "C" void ietidp_default_options(ietidp_options* o) {
     o->saddle_vcycles = 3;
     o->saddle_theta = 0.9;
     o->basis_method = IETIDP_BASIS_SZ;
+    o->mg_kind = IETIDP_MG_STANDARD;
 }
 
 // ---------------------------------------------------------------------------
@@ -102,7 +103,7 @@ static int build_topology(const iga_domain_desc* D, iga_problem* P) {
         long long n = 1;
         for (int r = 0; r < d; ++r) {
             if (pk.degree[r] < 1 || pk.degree[r] > IETI_MAXP - 1)
-                return fail(IETIDP_E_INVALID_ARG, "degree out of range [1,5] on patch " + std::to_string(k));
+                return fail(IETIDP_E_INVALID_ARG, "degree out of range [1,7] on patch " + std::to_string(k));
             if (pk.nelem[r] < 1) return fail(IETIDP_E_INVALID_ARG, "nelem < 1 on patch " + std::to_string(k));
             P->m[3 * k + r] = pk.nelem[r] + pk.degree[r];
             n *= P->m[3 * k + r];
@@ -254,6 +255,7 @@ extern "C" int iga_assemble_patches(const iga_domain_desc* D, void* stream, iga_
     auto* P = new iga_problem();
     P->stream = (cudaStream_t)stream;
     P->mem.st = P->stream;
+    if (D->ninterface > 0) P->interfaces.assign(D->interfaces, D->interfaces + D->ninterface);
     int rc = build_topology(D, P);
     if (rc != IETIDP_OK) {
         delete P;
@@ -480,6 +482,20 @@ SolveArgs ieti_solve_args(const ietidp_handle* h, int mode, const double* in, do
         return e ? std::atoi(e) : 0;
     }();
     a.kflags = kflags;
+    if (h->d_ho) {
+        const ietidp_handle* s = h->ho_sub;
+        a.ho = h->d_ho;
+        a.ho64 = h->ho64;
+        a.ho32 = h->ho32;
+        a.sub_pd = s->d_pd;
+        a.sub_K64 = s->K64;
+        a.sub_K32 = s->K32;
+        a.sub_tab = s->tab;
+        a.sub_tabf = s->tabf;
+        a.sub_itab = s->itab;
+        a.sub_A0inv64 = s->A0inv64;
+        a.sub_A0inv32 = s->A0inv32;
+    }
     if (mode == MODE_NEUMANN && h->opt.method == IETIDP_METHOD_DMG) a.mode = MODE_NEUMANN_DIRECT;
     return a;
 }
@@ -529,7 +545,8 @@ static int make_groups(ietidp_handle* h, const std::vector<SlotDesc>& slots, std
     const bool force_generic = fg && fg[0] == '1';
     for (const SlotDesc& sd : slots) {
         const PatchDesc& P = h->pd[sd.patch];
-        int gen = (force_generic || !solve_variant_exists(P.dim, P.p[0], P.p[1], P.p[2], mixed))
+        // the high-order V-cycle exists in the run-time-degree kernel only
+        int gen = (force_generic || h->d_ho || !solve_variant_exists(P.dim, P.p[0], P.p[1], P.p[2], mixed))
                       ? 2
                       : (solve_smem_min(P, mixed) > kSmemCap ? 1 : 0);
         by[std::make_tuple(P.dim, P.p[0], P.p[1], P.p[2], gen)].push_back(sd);
@@ -569,7 +586,8 @@ extern "C" int ietidp_setup(const iga_problem* P, const ietidp_options* opt_in, 
     if ((opt.method != IETIDP_METHOD_DUAL && opt.method != IETIDP_METHOD_SADDLE && opt.method != IETIDP_METHOD_DMG) ||
         opt.saddle_vcycles < 1 ||
         !(opt.saddle_theta > 0 && opt.saddle_theta < 1) ||
-        (opt.basis_method != IETIDP_BASIS_SZ && opt.basis_method != IETIDP_BASIS_NULLSPACE))
+        (opt.basis_method != IETIDP_BASIS_SZ && opt.basis_method != IETIDP_BASIS_NULLSPACE) ||
+        (opt.mg_kind != IETIDP_MG_STANDARD && opt.mg_kind != IETIDP_MG_HIGHORDER))
         return fail(IETIDP_E_INVALID_ARG, "bad method options");
     auto t0 = std::chrono::steady_clock::now();
     static std::atomic<unsigned long long> g_serial{0};
@@ -581,6 +599,8 @@ extern "C" int ietidp_setup(const iga_problem* P, const ietidp_options* opt_in, 
     h->mem.st = h->st;
     int rc = IETIDP_OK;
     auto bail = [&](int code) {
+        if (h->ho_sub) ietidp_destroy(h->ho_sub);
+        if (h->ho_prob) iga_problem_free(h->ho_prob);
         h->mem.release();
         if (h->h_pinned) cudaFreeHost(h->h_pinned);
         delete h;
@@ -607,6 +627,31 @@ extern "C" int ietidp_setup(const iga_problem* P, const ietidp_options* opt_in, 
     // up here (where allocating is allowed) commits the array's memory under
     // lazy module loading, so that ietidp_vcycles_noalloc never does
     CUH(ieti_noalloc_address(&h->noalloc_base));
+    // ---- high-order multigrid: the companion degree-1 problem --------------
+    // Sec. 4: below the finest level the hierarchy continues with splines of
+    // degree 1 on half the elements of every direction (same geometry map and
+    // patch layout, so the interfaces stay conforming); its standard
+    // hierarchies (both side masks) are those of a handle of its own
+    if (opt.mg_kind == IETIDP_MG_HIGHORDER) {
+        std::vector<iga_patch_desc> p1(P->patches);
+        for (auto& q : p1)
+            for (int r = 0; r < P->dim; ++r) {
+                q.degree[r] = 1;
+                q.nelem[r] = std::max(1, q.nelem[r] / 2);
+            }
+        iga_domain_desc D1{};
+        D1.dim = P->dim;
+        D1.npatch = P->npatch;
+        D1.patches = p1.data();
+        D1.ninterface = (int)P->interfaces.size();
+        D1.interfaces = P->interfaces.empty() ? nullptr : P->interfaces.data();
+        D1.rhs_kind = IGA_RHS_NONE;
+        CKH(iga_assemble_patches(&D1, stream, &h->ho_prob));
+        ietidp_options o1 = opt;
+        o1.mg_kind = IETIDP_MG_STANDARD;
+        o1.method = IETIDP_METHOD_DUAL;
+        CKH(ietidp_setup(h->ho_prob, &o1, stream, &h->ho_sub));
+    }
     // ---- primal objects and constraint rows -------------------------------
     // object kind of a class: number of directions in which its first copy
     // lies on the patch boundary
@@ -852,6 +897,14 @@ extern "C" int ietidp_setup(const iga_problem* P, const ietidp_options* opt_in, 
     bool mixed = opt.precision == IETIDP_PREC_MIXED;
     // ---- device memory -------------------------------------------------------
     CKH(h->mem.upload(&h->d_pd, h->pd, st));
+    if (opt.mg_kind == IETIDP_MG_HIGHORDER) {
+        std::vector<double> pool;
+        CKH(ieti_ho_build(P, h->pd, opt.alpha_reg, h->ho, pool));
+        std::vector<float> pool32(pool.begin(), pool.end());
+        CKH(h->mem.upload(&h->d_ho, h->ho, st));
+        CKH(h->mem.upload(&h->ho64, pool, st));
+        CKH(h->mem.upload(&h->ho32, pool32, st));
+    }
     // value pools: 16 elements of tail padding, since the local solver reads
     // color blocks widened to 16-byte boundaries (bulk prefetches)
     CKH(h->mem.alloc(&h->K64, koff + 16));
@@ -988,8 +1041,15 @@ extern "C" int ietidp_setup(const iga_problem* P, const ietidp_options* opt_in, 
     {
         // slot s serves basis row s (if s < nrows) and patch s (if s < N)
         std::vector<long long> cgo(nslots_max), lvo(nslots_max);
+        // high-order multigrid: x | b | r of the patch's levels, then those of
+        // the degree-1 hierarchy, then two work tensors of the fine free grid
         auto lvneed = [&](const PatchDesc& q) {
-            return std::max<long long>(3LL * q.nlvec, (long long)q.nlx + q.nlb + q.n + 4);
+            long long need = std::max<long long>(3LL * q.nlvec, (long long)q.nlx + q.nlb + q.n + 4);
+            if (h->ho_sub) {
+                const int k = (int)(&q - h->pd.data());
+                need = std::max(need, 3LL * q.nlvec + 3LL * h->ho_sub->pd[k].nlvec + 2LL * q.n);
+            }
+            return need;
         };
         for (int s = 0; s < nslots_max; ++s) {
             long long n = 0, nl = 0;
@@ -1315,6 +1375,8 @@ extern "C" int ietidp_destroy(ietidp_handle* h) {
     for (auto& sd : h->side) cudaStreamDestroy(sd);
     for (auto& ev : h->join) cudaEventDestroy(ev);
     if (h->fork) cudaEventDestroy(h->fork);
+    if (h->ho_sub) ietidp_destroy(h->ho_sub);
+    if (h->ho_prob) iga_problem_free(h->ho_prob);
     delete h;
     return IETIDP_OK;
 }

@@ -104,6 +104,18 @@ enum SlotMode {
     MODE_VCYCLE_DIR = 9       // V-cycles on the Dirichlet hierarchy (K_II, every side masked)
 };
 
+// High-order multigrid of one patch (Sec. 4, p >= 4), per hierarchy kind
+// (0 Neumann, 1 Dirichlet) and direction: free fine functions (count, first
+// index), free functions of the degree-1 space on half the elements, and the
+// offsets in the pool of the fast-diagonalization eigenvectors U (nf x nf,
+// U[j + nf i] = eigenvector i at function j), of the L2-projection
+// prolongation P (nf x nc, P[j + nf c]) and of 1 / eigenvalue sums (tensor
+// nf0 x nf1 x nf2, first direction fastest).
+struct HoDesc {
+    int nf[2][3], lof[2][3], nc[2][3], loc[2][3];
+    long long u[2][3], pt[2][3], dinv[2];
+};
+
 struct SolveArgs {
     const PatchDesc* pd;
     const SlotDesc* slots;
@@ -153,6 +165,21 @@ struct SolveArgs {
     // [start, end] of the launch in globaltimer nanoseconds (or null): thread
     // 0 of every CTA lowers the start at entry and raises the end at exit
     unsigned long long* tspan;
+    // high-order multigrid (null: the standard hierarchy): per-patch
+    // descriptors and pools (FP64 / FP32), and the degree-1 hierarchies of
+    // the companion problem (patch descriptors and value, table and
+    // coarsest-inverse pools)
+    const HoDesc* ho;
+    const double* ho64;
+    const float* ho32;
+    const PatchDesc* sub_pd;
+    const double* sub_K64;
+    const float* sub_K32;
+    const double* sub_tab;
+    const float* sub_tabf;
+    const int* sub_itab;
+    const double* sub_A0inv64;
+    const float* sub_A0inv32;
     // kernel variant switches for measurements (IETIDP_KFLAGS, 0 = all on):
     // 4 FP64 operator reads its input from global memory, 16 no L2 prefetch
     // of streamed color blocks, 32 the mixed path's stiffness operator in

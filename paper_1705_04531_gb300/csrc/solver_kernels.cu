@@ -98,6 +98,16 @@ struct VCycle {
     const T* A0inv;   // coarsest inverse
     T* lvec;          // this slot's level vectors: x | b | r, each nlvec
     int nlvec;
+    // high-order multigrid (Sec. 4, p >= 4): null for the standard V-cycle;
+    // else the patch's descriptor, the hierarchy kind, the operator pool, the
+    // degree-1 hierarchy below the finest level and two work tensors of the
+    // fine free grid
+    const HoDesc* ho = nullptr;
+    int hkind = 0;
+    const T* hpool = nullptr;
+    const VCycle<T>* coarse = nullptr;
+    T* t1 = nullptr;
+    T* t2 = nullptr;
 
     __device__ T* X(int l) const { return lvec + P->lev[l].voff; }
     __device__ T* B(int l) const { return lvec + nlvec + P->lev[l].voff; }
@@ -313,14 +323,147 @@ struct Slot {
     double *x, *r, *z, *p, *q;
 };
 
+// out = in x_r W along direction r of a tensor with extents din (first
+// direction fastest): out[.., a, ..] = sum_b W(a, b) in[.., b, ..] with
+// W(a, b) = W[b + ldW a] (trans) or W[a + ldW b]; direction r gets extent nout
 template <typename T>
-__device__ void vcycle_apply(const VCycle<T>& vc, const double* rin, double* zout, int nu1, int nu2) {
+__device__ void mode_prod(const T* in, T* out, const int* din, int r, int nout, const T* W, int ldW, bool trans) {
+    int dout[3] = {din[0], din[1], din[2]};
+    dout[r] = nout;
+    const int total = dout[0] * dout[1] * dout[2];
+    const int sin = r == 0 ? 1 : (r == 1 ? din[0] : din[0] * din[1]);
+    const int nin = din[r];
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const int i0 = idx % dout[0], rem = idx / dout[0], i1 = rem % dout[1], i2 = rem / dout[1];
+        const int a = r == 0 ? i0 : (r == 1 ? i1 : i2);
+        const T* line = in + (r == 0 ? 0 : i0) + din[0] * ((r == 1 ? 0 : i1) + din[1] * (r == 2 ? 0 : i2));
+        T acc = 0;
+        if (trans)
+            for (int b = 0; b < nin; ++b) acc += W[b + (long long)ldW * a] * line[(long long)b * sin];
+        else
+            for (int b = 0; b < nin; ++b) acc += W[a + (long long)ldW * b] * line[(long long)b * sin];
+        out[idx] = acc;
+    }
+    __syncthreads();
+}
+
+// the free sub-grid (first index lo_r, extent n_r per direction) of a full
+// natural grid with extents m: gather into a tensor / add a tensor back
+template <typename T>
+__device__ void free_gather(const T* full, const int* m, const int* lo, const int* n, T* t) {
+    const int total = n[0] * n[1] * n[2];
+    for (int j = threadIdx.x; j < total; j += blockDim.x) {
+        const int j0 = j % n[0], rem = j / n[0], j1 = rem % n[1], j2 = rem / n[1];
+        t[j] = full[(j0 + lo[0]) + m[0] * ((j1 + lo[1]) + m[1] * (j2 + lo[2]))];
+    }
+    __syncthreads();
+}
+template <typename T>
+__device__ void free_add(T* full, const int* m, const int* lo, const int* n, const T* t) {
+    const int total = n[0] * n[1] * n[2];
+    for (int j = threadIdx.x; j < total; j += blockDim.x) {
+        const int j0 = j % n[0], rem = j / n[0], j1 = rem % n[1], j2 = rem / n[1];
+        full[(j0 + lo[0]) + m[0] * ((j1 + lo[1]) + m[1] * (j2 + lo[2]))] += t[j];
+    }
+    __syncthreads();
+}
+
+// x_fine += L^-1 r_fine: fast diagonalization of the Kronecker-sum smoother
+// of the finest level (U^T along every direction, scaling, U back)
+template <typename T>
+__device__ void ho_smooth(const VCycle<T>& vc) {
+    const HoDesc& H = *vc.ho;
+    const int kd = vc.hkind, d = vc.P->dim;
+    const LevelDesc& F = vc.P->lev[vc.P->L - 1];
+    int dims[3] = {H.nf[kd][0], H.nf[kd][1], H.nf[kd][2]};
+    free_gather(vc.R(vc.P->L - 1), F.m, H.lof[kd], dims, vc.t1);
+    T* cur = vc.t1;
+    T* oth = vc.t2;
+    for (int r = 0; r < d; ++r) {
+        mode_prod(cur, oth, dims, r, dims[r], vc.hpool + H.u[kd][r], dims[r], true);
+        T* t = cur;
+        cur = oth;
+        oth = t;
+    }
+    const T* Dinv = vc.hpool + H.dinv[kd];
+    for (int j = threadIdx.x; j < dims[0] * dims[1] * dims[2]; j += blockDim.x) cur[j] *= Dinv[j];
+    __syncthreads();
+    for (int r = 0; r < d; ++r) {
+        mode_prod(cur, oth, dims, r, dims[r], vc.hpool + H.u[kd][r], dims[r], false);
+        T* t = cur;
+        cur = oth;
+        oth = t;
+    }
+    free_add(vc.X(vc.P->L - 1), F.m, H.lof[kd], dims, cur);
+}
+
+// high-order V-cycle: smoothing on the finest level, L2-projection transfer
+// to the degree-1 hierarchy and its standard V-cycle, back, smoothing
+template <typename T>
+__device__ void ho_run(const VCycle<T>& vc, int nu1, int nu2) {
+    const HoDesc& H = *vc.ho;
+    const int kd = vc.hkind, d = vc.P->dim, L = vc.P->L;
+    const LevelDesc& F = vc.P->lev[L - 1];
+    T* x = vc.X(L - 1);
+    for (int i = threadIdx.x; i < F.n; i += blockDim.x) x[i] = 0;
+    __syncthreads();
+    for (int s = 0; s < nu1; ++s) {
+        vc.residual(L - 1);
+        ho_smooth(vc);
+    }
+    vc.residual(L - 1);
+    // restriction P^T r into the right-hand side of the degree-1 hierarchy
+    const VCycle<T>& cv = *vc.coarse;
+    const int Lc = cv.P->L;
+    const LevelDesc& Cf = cv.P->lev[Lc - 1];
+    int dims[3] = {H.nf[kd][0], H.nf[kd][1], H.nf[kd][2]};
+    free_gather(vc.R(L - 1), F.m, H.lof[kd], dims, vc.t1);
+    T* cur = vc.t1;
+    T* oth = vc.t2;
+    for (int r = 0; r < d; ++r) {
+        mode_prod(cur, oth, dims, r, H.nc[kd][r], vc.hpool + H.pt[kd][r], H.nf[kd][r], true);
+        dims[r] = H.nc[kd][r];
+        T* t = cur;
+        cur = oth;
+        oth = t;
+    }
+    T* bc = cv.B(Lc - 1);
+    for (int i = threadIdx.x; i < Cf.n; i += blockDim.x) bc[i] = 0;
+    __syncthreads();
+    free_add(bc, Cf.m, H.loc[kd], dims, cur);
+    cv.run(2, 2);
+    // prolongation P x_c
+    free_gather(cv.X(Lc - 1), Cf.m, H.loc[kd], dims, vc.t1);
+    cur = vc.t1;
+    oth = vc.t2;
+    for (int r = 0; r < d; ++r) {
+        mode_prod(cur, oth, dims, r, H.nf[kd][r], vc.hpool + H.pt[kd][r], H.nf[kd][r], false);
+        dims[r] = H.nf[kd][r];
+        T* t = cur;
+        cur = oth;
+        oth = t;
+    }
+    free_add(x, F.m, H.lof[kd], dims, cur);
+    for (int s = 0; s < nu2; ++s) {
+        vc.residual(L - 1);
+        ho_smooth(vc);
+    }
+}
+
+// one call per application (not inlined at the nine call sites of the kernel:
+// a V-cycle is long enough that the call costs nothing, and inlining both
+// hierarchies' V-cycles at every site multiplies the compile time)
+template <typename T>
+__device__ __noinline__ void vcycle_apply(const VCycle<T>& vc, const double* rin, double* zout, int nu1, int nu2) {
     int L = vc.P->L;
     int n = vc.P->lev[L - 1].n;
     T* b = vc.B(L - 1);
     for (int i = threadIdx.x; i < n; i += blockDim.x) b[i] = (T)rin[i];
     __syncthreads();
-    vc.run(nu1, nu2);
+    if (vc.ho)
+        ho_run(vc, nu1, nu2);
+    else
+        vc.run(nu1, nu2);
     const T* x = vc.X(L - 1);
     for (int i = threadIdx.x; i < n; i += blockDim.x) zout[i] = (double)x[i];
     __syncthreads();
@@ -414,6 +557,28 @@ __global__ void __launch_bounds__(512) k_solve(SolveArgs a0) {
     vc.A0inv = (a.mixed ? (const T*)(const void*)a.A0inv32 : (const T*)(const void*)a.A0inv64) + P.a0off[kind];
     vc.lvec = (T*)a.lv + sd.lv;
     vc.nlvec = P.nlvec;
+    // high-order multigrid: the degree-1 hierarchy of the companion problem
+    // (same patch index) and the work tensors follow the slot's x | b | r
+    VCycle<T> vco;
+    if (a.ho) {
+        const PatchDesc& Q = a.sub_pd[sd.patch];
+        vco.P = &Q;
+        vco.mask = vc.mask;
+        vco.alpha = vc.alpha;
+        vco.K = a.mixed ? (const T*)(const void*)a.sub_K32 : (const T*)(const void*)a.sub_K64;
+        vco.tab = a.mixed ? (const T*)(const void*)a.sub_tabf : (const T*)(const void*)a.sub_tab;
+        vco.itab = a.sub_itab;
+        vco.A0inv = (a.mixed ? (const T*)(const void*)a.sub_A0inv32 : (const T*)(const void*)a.sub_A0inv64) +
+                    Q.a0off[kind];
+        vco.lvec = vc.lvec + 3 * (long long)P.nlvec;
+        vco.nlvec = Q.nlvec;
+        vc.ho = a.ho + sd.patch;
+        vc.hkind = kind;
+        vc.hpool = a.mixed ? (const T*)(const void*)a.ho32 : (const T*)(const void*)a.ho64;
+        vc.coarse = &vco;
+        vc.t1 = vco.lvec + 3 * (long long)Q.nlvec;
+        vc.t2 = vc.t1 + n;
+    }
     long long vcount = 0;
 
     if (a.mode == MODE_SCHUR) {

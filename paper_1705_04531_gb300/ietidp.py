@@ -65,7 +65,7 @@ class ietidp_options(C.Structure):
                 ("maxit_inner", C.c_int), ("nu_pre", C.c_int), ("nu_post", C.c_int),
                 ("coarse_elems", C.c_int), ("dirichlet_vcycles", C.c_int), ("alpha_reg", C.c_double),
                 ("cluster", C.c_int), ("method", C.c_int), ("saddle_vcycles", C.c_int),
-                ("saddle_theta", C.c_double), ("basis_method", C.c_int)]
+                ("saddle_theta", C.c_double), ("basis_method", C.c_int), ("mg_kind", C.c_int)]
 
 
 class ietidp_stats(C.Structure):
@@ -225,6 +225,8 @@ def default_options(**kw) -> ietidp_options:
             v = METHOD[v]
         if k == "basis_method" and isinstance(v, str):
             v = BASIS[v]
+        if k == "mg_kind" and isinstance(v, str):
+            v = {"standard": 0, "highorder": 1}[v]
         setattr(o, k, v)
     return o
 
