@@ -183,7 +183,8 @@ struct SolveArgs {
     // kernel variant switches for measurements (IETIDP_KFLAGS, 0 = all on):
     // 4 FP64 operator reads its input from global memory, 16 no L2 prefetch
     // of streamed color blocks, 32 the mixed path's stiffness operator in
-    // FP64 instead of FP32 pairs
+    // FP64 instead of FP32 pairs, 128 that operator with its input in
+    // natural order instead of the color-major ghost-padded layout
     int kflags;
 };
 

@@ -709,6 +709,113 @@ __device__ __noinline__ void spmv_df(const PatchDesc& P, const float* __restrict
     IETI_T1(49);
 }
 
+// The same operator with its input staged in the color-major, ghost-padded
+// layout of the V-cycle vectors (color block c at c * blk, row (t0, t1, t2)
+// of the block at (t0+1) + xk0 (t1+1) + xk0 xk1 (t2+1), zeros in the ghost
+// layer): a warp's rows of one color read consecutive pairs (no bank
+// conflicts) and every neighbour lies at a fixed offset per color (no bounds
+// tests).  Rows are visited in storage order, each thread advancing its color
+// as its row index passes the color's end; thread 0 moves the color blocks two
+// colors ahead into L2 (bulk prefetch) as it enters each color.  `ct`: the
+// fine level's color table; needs NC * blk pairs of staging space.
+template <int D, int P0, int P1, int P2>
+__device__ __noinline__ void spmv_df_cm(const PatchDesc& P, const CTab* __restrict__ ct, const float* __restrict__ Khi,
+                                        const float* __restrict__ Klo, const double* x, double* y, int rowmask,
+                                        const double* sub, double scale, int only, long long* phase, int xs_off,
+                                        bool prefetch) {
+    constexpr int W0 = 2 * P0 + 1, W1 = 2 * P1 + 1, W2 = 2 * P2 + 1, S = W0 * W1 * W2;
+    constexpr int C0 = P0 + 1, C1 = P1 + 1, C2 = P2 + 1, NC = C0 * C1 * C2;
+    const LevelDesc& F = P.lev[P.L - 1];
+    const int m0 = F.m[0], m1 = F.m[1], m2 = F.m[2];
+    const int blk = F.blk, xk0 = F.xk[0], xk1 = F.xk[1], xk01 = xk0 * xk1;
+    IETI_T0();
+    float2* xs = reinterpret_cast<float2*>(shm<double>(xs_off));
+    for (int e = threadIdx.x; e < NC * blk; e += blockDim.x) {
+        const int c = e / blk, w = e - c * blk;
+        const int c0 = c % C0, c1 = (c / C0) % C1, c2 = c / (C0 * C1);
+        const int t0 = w % xk0 - 1, t1 = (w / xk0) % xk1 - 1, t2 = D == 3 ? w / xk01 - 1 : 0;
+        const int i0 = c0 + C0 * t0, i1 = c1 + C1 * t1, i2 = c2 + C2 * t2;
+        const bool in = t0 >= 0 && i0 < m0 && t1 >= 0 && i1 < m1 && (D < 3 || (t2 >= 0 && i2 < m2));
+        const double v = in ? x[i0 + m0 * (i1 + m1 * i2)] : 0.0;
+        const float hi = (float)v;
+        xs[e] = make_float2(hi, (float)(v - (double)hi));
+    }
+    constexpr long long A = 4;   // 16 bytes of FP32
+    auto prefetch_color = [&](int c) {
+        if (!prefetch || c >= NC) return;
+        const CTab t = ct[c];
+        const long long s0 = F.koff + (long long)t.off * S;
+        const long long len = (long long)t.k0 * t.k1 * t.k2 * S;
+        const long long lo = s0 & ~(A - 1), hi = (s0 + len + A - 1) & ~(A - 1);
+        bulk_prefetch_l2(Khi + lo, (unsigned)((hi - lo) * 4));
+        bulk_prefetch_l2(Klo + lo, (unsigned)((hi - lo) * 4));
+    };
+    if (threadIdx.x == 0) {
+        prefetch_color(0);
+        prefetch_color(1);
+    }
+    __syncthreads();
+    int c = -1, off = 0, cnt = 0, end = 0;
+    for (int s = threadIdx.x; s < F.n; s += blockDim.x) {
+        while (s >= end) {
+            ++c;
+            const CTab t = ct[c];
+            off = t.off;
+            cnt = t.k0 * t.k1 * t.k2;
+            end = off + cnt;
+            if (threadIdx.x == 0) prefetch_color(c + 2);
+        }
+        const CTab t = ct[c];
+        const int c0 = c % C0, c1 = (c / C0) % C1, c2 = c / (C0 * C1);
+        const int q = s - off;
+        const int t0 = q % t.k0, tr = q / t.k0;
+        const int t1 = tr % t.k1, t2 = tr / t.k1;
+        const int i0 = c0 + C0 * t0, i1 = c1 + C1 * t1, i2 = c2 + C2 * t2;
+        const int i = i0 + m0 * (i1 + m1 * i2);
+        bool take = !ieti_masked(rowmask, F.m, i0, i1, i2);
+        if (only == 1) take = take && ieti_on_boundary(F.m, D, i0, i1, i2) && !ieti_masked(P.dmask, F.m, i0, i1, i2);
+        double v = 0.0;
+        if (take) {
+            int e0[W0], e1[W1], e2[W2];
+#pragma unroll
+            for (int o = -P0; o <= P0; ++o) {
+                const int dd = (c0 + o + C0) / C0 - 1;
+                e0[o + P0] = (o - C0 * dd) * blk + dd;
+            }
+#pragma unroll
+            for (int o = -P1; o <= P1; ++o) {
+                const int dd = (c1 + o + C1) / C1 - 1;
+                e1[o + P1] = (o - C1 * dd) * C0 * blk + dd * xk0;
+            }
+#pragma unroll
+            for (int o = -P2; o <= P2; ++o) {
+                const int dd = (c2 + o + C2) / C2 - 1;
+                e2[o + P2] = D == 3 ? (o - C2 * dd) * C0 * C1 * blk + dd * xk01 : 0;
+            }
+            const float2* X = xs + c * blk + (t0 + 1) + xk0 * (t1 + 1) + (D == 3 ? xk01 * (t2 + 1) : 0);
+            float sh[2] = {0.f, 0.f}, sc[2] = {0.f, 0.f};
+            const long long base = F.koff + (long long)off * S + q;
+#pragma unroll
+            for (int o = 0; o < S; ++o) {
+                const int o0 = o % W0, o1 = (o / W0) % W1, o2 = o / (W0 * W1);
+                const float2 xv = X[e0[o0] + e1[o1] + e2[o2]];
+                const float ah = __ldg(Khi + base + (long long)o * cnt);
+                const float al = __ldg(Klo + base + (long long)o * cnt);
+                const float pr = ah * xv.x;
+                const float pe = fmaf(ah, xv.x, -pr);
+                const float cr = fmaf(ah, xv.y, al * xv.x);
+                df_add(sh[o & 1], sc[o & 1], pr, pe + cr);
+            }
+            df_add(sh[0], sc[0], sh[1], sc[1]);
+            v = scale * ((double)sh[0] + (double)sc[0]);
+        }
+        if (sub) v = sub[i] + v;
+        y[i] = v;
+    }
+    __syncthreads();
+    IETI_T1(49);
+}
+
 template <typename T, int D, int P0, int P1, int P2, bool XG>
 __device__ void vcycle_apply(const VC<T, D, P0, P1, P2, XG>& vc, const double* rin, double* zout, int nu1, int nu2) {
     const int L = vc.P->L;
@@ -867,8 +974,15 @@ __global__ void __launch_bounds__(512) k_solve_t(SolveArgs a0) {
     // the stiffness operator of the solve phase (CG, Schur complement,
     // V-cycle residuals): on the mixed path in FP32-pair arithmetic, else FP64
     const bool df = sizeof(T) == 4 && xs_off >= 0 && a.K32lo && !(a.kflags & 32);
+    // the color-major staging takes NC blk pairs; the vector area holds at
+    // least nlx + nlb + n FP32 values
+    const bool dfcm = df && !(a.kflags & 128) &&
+                      (size_t)ieti_ncolors(P.p) * F.blk * 8 <= (size_t)vec_elems(P) * sizeof(T);
     auto opK = [&](const double* in, double* out, int rmask, const double* sb, double sc, int only, long long* ph) {
-        if (df)
+        if (dfcm)
+            spmv_df_cm<D, P0, P1, P2>(P, vc.ct + (P.L - 1) * ieti_ncolors(P.p), a.K32, a.K32lo, in, out, rmask, sb,
+                                      sc, only, ph, xs_off, !(a.kflags & 16));
+        else if (df)
             spmv_df<D, P0, P1, P2>(P, a.K32, a.K32lo, in, out, rmask, sb, sc, only, ph, xs_off);
         else
             spmv64<D, P0, P1, P2>(P, a.K64, in, out, rmask, sb, sc, only, ph, xs_off);
