@@ -57,11 +57,14 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--vcycle-reps", type=int, default=50)
-    ap.add_argument("--mode", default="bench", choices=["bench", "vcycle", "serve", "profile"],
+    ap.add_argument("--mode", default="bench", choices=["bench", "vcycle", "serve", "profile", "phases"],
                     help="vcycle: setup plus three batched V-cycle launches (profiling target); "
                          "serve: Poisson-arrival request stream through the continuous-batching server; "
                          "profile: one batched solve of --batch copies inside a profiler range "
-                         "(cudaProfilerStart/Stop), after a warm-up solve")
+                         "(cudaProfilerStart/Stop), after a warm-up solve; "
+                         "phases: per-phase times of a batched V-cycle (library built with "
+                         "IETIDP_PHASE_TIMERS=1)")
+    ap.add_argument("--sm-mhz", type=float, default=2070.0, help="phases: SM clock for cycle counts")
     ap.add_argument("--rate", type=float, default=None, help="serve: arrivals per second (one rate)")
     ap.add_argument("--nreq", type=int, default=512, help="serve: requests in the stream")
     ap.add_argument("--concurrency", type=int, default=8, help="serve: worker streams")
@@ -447,6 +450,55 @@ def extra_workload(api, torch, name, B, steps, warmup, flush, stream, peak):
     return out
 
 
+def highorder_compare(api, torch, flush, stream, steps=2):
+    """The paper's high-degree settings (Sec. 4; p = 4 and 7 in Tables 1 and
+    2): quarter annulus 6x6, n = 32, one solve at a time, with the high-order
+    multigrid (degree 1 below the finest level, subspace-corrected mass
+    smoother; mixed and FP64 paths) and with the standard one (degree p on
+    every level, Gauss-Seidel; mixed path); accuracy against the FP64
+    high-order solve.  A set-up or solve that does not converge within the
+    default iteration caps is reported as such."""
+    out = {}
+    for p_ in (4, 7):
+        dom = W.annulus_6x6(32, p_)
+        prob = api.Problem(dom)
+        ref = api.Solver(prob, precision="fp64", mg_kind="highorder")
+        uref, _ = ref.solve()
+        torch.cuda.synchronize()
+        uref_p = ref.split(uref)
+        ref.close()
+        res = {"patches": dom.npatch, "degree": p_, "elements_per_patch": "32x32",
+               "torn_dofs": int(sum(dom.patch_ndof(k) for k in range(dom.npatch)))}
+        for kind, prec in (("highorder", "mixed"), ("highorder", "fp64"), ("standard", "mixed")):
+            key = f"{kind}_{prec}"
+            try:
+                t0 = time.perf_counter()
+                sol = api.Solver(prob, precision=prec, mg_kind=kind)
+                torch.cuda.synchronize()
+                setup_ms = 1e3 * (time.perf_counter() - t0)
+                u, st = sol.solve()
+            except api.IetidpError as e:
+                res[key] = {"failed": str(e)}
+                continue
+            lat = []
+            for _ in range(steps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                flush.zero_()
+                e0.record(stream)
+                u, st = sol.solve(None, u)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                lat.append(e0.elapsed_time(e1))
+            res[key] = {"solves_per_s": 1e3 / float(np.median(lat)), "p50_ms": float(np.median(lat)),
+                         "outer_it": st["outer_it"], "inner_it_avg": st["inner_it_avg"],
+                         "converged": bool(st["converged"]),
+                         "rel_err_vs_fp64_highorder": relerr(sol.split(u), uref_p), "setup_ms": setup_ms}
+            sol.close()
+        prob.close()
+        out[dom.name] = res
+    return out
+
+
 def serve_stream(api, torch, nreq, rate, seed, concurrency, budget_gb, precision="mixed", method="dual"):
     """Poisson-arrival request stream through the continuous-batching server:
     solves/s, p50/p99 latency (arrival to result) and the peak of the
@@ -534,6 +586,37 @@ def run_vcycle_probe(args):
                       "x_norm": float(x.norm())}))
 
 
+def run_phases(args):
+    """Phase breakdown of one batched V-cycle (--batch copies of the
+    workload, Neumann hierarchies of every patch, plus the fine operator of
+    the CG) from the in-kernel clock counters of CTA 0 (a library built with
+    IETIDP_PHASE_TIMERS=1; all zero otherwise): microseconds per V-cycle at
+    the SM clock given by --sm-mhz, averaged over ten launches."""
+    import torch
+    from paper_1705_04531_gb300 import build
+    build.build()
+    from paper_1705_04531_gb300 import ietidp as api
+    dom = workload(args.workload)
+    probs = [api.Problem(dom) for _ in range(args.batch)]
+    sols = [api.Solver(p_, precision=args.precision) for p_ in probs]
+    api.Solver.solve_batch(sols)        # autotuning of the merged launches
+    fs = [p_.load() for p_ in probs]
+    xs = [torch.zeros_like(f) for f in fs]
+    for _ in range(2):
+        api.Solver.vcycles_batch(sols, fs, xs, 1)
+    q0 = sols[0].phase_timers()
+    ms = [api.Solver.vcycles_batch(sols, fs, xs, 1) for _ in range(10)]
+    q1 = sols[0].phase_timers()
+    dq = (q1 - q0) / 10 / args.sm_mhz
+    names = {48: "coarsest", 49: "fine_operator"}
+    for l in range(1, 12):
+        for k, nm in enumerate(["sweeps", "residual", "restrict", "prolong"]):
+            names[4 * l + k] = f"level{l}_{nm}"
+    print(json.dumps({"mode": "phases", "workload": args.workload, "batch": args.batch,
+                      "precision": args.precision, "launch_ms": float(np.median(ms)),
+                      "phase_us": {names[i]: round(float(dq[i]), 1) for i in sorted(names) if dq[i] != 0}}))
+
+
 def run_serve(args):
     """Serving stream (m x m unit-square patch grids, m in {2,4,6,8}, p in
     {2,3}, 16..128 elements per patch direction, f = 8 random sine modes,
@@ -592,6 +675,8 @@ def main():
         return run_serve(args)
     if args.mode == "profile":
         return run_profile(args)
+    if args.mode == "phases":
+        return run_phases(args)
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -708,13 +793,14 @@ def main():
     peak, peak_kind = peaks()
     # the other workloads of the benchmark family and the serving stream
     # (single process only: with several ranks the line reports the headline)
-    extra, serve = {}, []
+    extra, serve, highorder = {}, [], None
     if world == 1 and not args.no_extra:
         xs_ = min(args.steps, 5)
         for nm, B in (("square2x2_p2_n16", 8), ("uneven8x8_s0", 2), ("cube2x2x2_p2_n32", 4)):
             extra[nm] = extra_workload(api, torch, nm, B, xs_, 2, flush, stream, peak)
         for r_ in [float(v) for v in args.serve_rates.split(",") if v]:
             serve.append(serve_stream(api, torch, args.nreq, r_, 0, args.concurrency, args.budget_gb))
+        highorder = highorder_compare(api, torch, flush, stream)
     tune = api.autotune_table()
 
     if rank != 0:
@@ -778,6 +864,8 @@ def main():
     }
     if extra:
         line["workloads"] = extra
+    if highorder:
+        line["highorder"] = highorder
     if serve:
         line["serve"] = {"stream": f"{args.nreq} requests, m x m unit-square patches, m in {{2,4,6,8}}, p in {{2,3}}, "
                                    "n in {16,32,64,128}, f = 8 random sine modes, Poisson arrivals",

@@ -292,7 +292,7 @@ class IETIDP:
 
     def _setup_mg(self):
         o = self.o
-        self.hier, self.mgN, self.mgD, self.phi = [], [], [], []
+        self.hier, self.mgN, self.mgD, self.phi, self.mgB = [], [], [], [], []
         d = self.dom.dim
         allsides = (1 << (2 * d)) - 1
         for k in range(self.N):
@@ -300,12 +300,19 @@ class IETIDP:
                                     self.dom.patch_degree(k), o.cmin)
             self.hier.append(h)
             alpha = o.alpha if self.floating[k] else 0.0
+            std = multigrid.MGOperator(h, self.dmask[k], alpha, o.nu1, o.nu2)
             if o.mg_kind == "highorder":
                 self.mgN.append(highorder.HighOrderMG(self.dom, k, self.Kfull[k], self.dmask[k], alpha))
                 self.mgD.append(highorder.HighOrderMG(self.dom, k, self.Kfull[k], allsides, 0.0))
             else:
-                self.mgN.append(multigrid.MGOperator(h, self.dmask[k], alpha, o.nu1, o.nu2))
+                self.mgN.append(std)
                 self.mgD.append(multigrid.MGOperator(h, allsides, 0.0, o.nu1, o.nu2))
+            # the primal basis (Eq. 6) is preconditioned by the standard
+            # V-cycle in both settings: Sec. 4 fixes only the tolerance of these
+            # local problems, and the high-order V-cycle, projected on ker C,
+            # needs more than the iteration cap for some constraint rows of the
+            # 6x6 quarter annulus (p = 4, n = 32)
+            self.mgB.append(std)
             self.phi.append(self._basis_mg(k))
 
     def _setup_mg_dirichlet(self):
@@ -338,7 +345,7 @@ class IETIDP:
         n = K.shape[0]
         phi = np.zeros((n, npi))
         PE = self._projector(k)
-        V = self.mgN[k].vcycle
+        V = self.mgB[k].vcycle
         for j in range(npi):
             psi = (C[j].toarray().ravel() != 0).astype(np.float64)
             b = -PE(K @ psi)

@@ -48,8 +48,19 @@ def _compile(src):
     return obj
 
 
+def _stamp():
+    return LIB + ".flags"
+
+
 def stale():
     if not os.path.exists(LIB):
+        return True
+    # built with other compile flags (debug bounds, phase timers)
+    try:
+        with open(_stamp()) as fh:
+            if fh.read() != " ".join(_flags()):
+                return True
+    except OSError:
         return True
     t = os.path.getmtime(LIB)
     deps = [os.path.join(SRC, f) for f in os.listdir(SRC)] + [os.path.join(HERE, "..", "include", "ietidp.h")]
@@ -68,6 +79,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(_stamp(), "w") as fh:
+        fh.write(" ".join(_flags()))
     if verbose:
         print("built", LIB, file=sys.stderr)
     return LIB

@@ -482,7 +482,14 @@ SolveArgs ieti_solve_args(const ietidp_handle* h, int mode, const double* in, do
         return e ? std::atoi(e) : 0;
     }();
     a.kflags = kflags;
-    if (h->d_ho) {
+    // the high-order multigrid serves the solve phase; the primal basis
+    // (Eq. 6) is computed with the patch's standard hierarchy, whose
+    // symmetric Gauss-Seidel V-cycle V satisfies V K <= 1 as the
+    // Schoeberl-Zulehner CG requires (K^ = (0.99 V)^-1 > K); the
+    // subspace-corrected mass smoother may overshoot (eigenvalues of V K up to
+    // 1 + its contraction rate), which makes K^ - K indefinite
+    const bool basis_mode = mode == MODE_BASIS || mode == MODE_SZW || mode == MODE_BASIS_SZ;
+    if (h->d_ho && !basis_mode) {
         const ietidp_handle* s = h->ho_sub;
         a.ho = h->d_ho;
         a.ho64 = h->ho64;
@@ -1134,15 +1141,19 @@ extern "C" int ietidp_setup(const iga_problem* P, const ietidp_options* opt_in, 
         if (fl & IETI_FLAG_NOT_SPD) return bail(fail(IETIDP_E_BREAKDOWN, "banded Cholesky: stiffness not SPD"));
     }
     // ---- primal basis (Eq. 6) ---------------------------------------------
+    // with the high-order multigrid the basis uses the standard hierarchy
+    // (see ieti_solve_args), whose V-cycle weakens with the degree: more
+    // iterations allowed there
+    const int basis_maxit = h->d_ho ? 8 * opt.maxit_inner : opt.maxit_inner;
     if (nslot_basis > 0) {
         if (sz) {
             // W = Khat^{-1} C^T per constraint row, Hhat^{-1} per patch, then SZ-CG
             CHK(run_solve(h, MODE_SZW, h->gbasis, nullptr, nullptr, 0.0, 0, h->vst + 8));
             cudaError_t e = launch_sz_hinv(h->d_pd, N, h->crow_ptr, h->c_idx, h->c_w, h->szW, h->szHinv, h->flags, st);
             if (e != cudaSuccess) return bail(fail(IETIDP_E_CUDA, std::string("SZ set-up: ") + cudaGetErrorString(e)));
-            CHK(run_solve(h, MODE_BASIS_SZ, h->gbasis, nullptr, nullptr, opt.tol_basis, opt.maxit_inner, h->vst + 8));
+            CHK(run_solve(h, MODE_BASIS_SZ, h->gbasis, nullptr, nullptr, opt.tol_basis, basis_maxit, h->vst + 8));
         } else {
-            CHK(run_solve(h, MODE_BASIS, h->gbasis, nullptr, nullptr, opt.tol_basis, opt.maxit_inner, h->vst + 8));
+            CHK(run_solve(h, MODE_BASIS, h->gbasis, nullptr, nullptr, opt.tol_basis, basis_maxit, h->vst + 8));
         }
         CUH(cudaStreamSynchronize(st));
         std::vector<int> its(nslot_basis);

@@ -184,7 +184,8 @@ struct SolveArgs {
     // 4 FP64 operator reads its input from global memory, 16 no L2 prefetch
     // of streamed color blocks, 32 the mixed path's stiffness operator in
     // FP64 instead of FP32 pairs, 128 that operator with its input in
-    // natural order instead of the color-major ghost-padded layout
+    // natural order instead of the color-major ghost-padded layout, 256 one
+    // lane per row in every color step (no lane groups on coarse levels)
     int kflags;
 };
 

@@ -254,6 +254,65 @@ struct VC {
         return (acc[0] + acc[1]) + (acc[2] + acc[3]);
     }
 
+    // G lanes per row (coarse levels: a color has at most blockDim / G rows;
+    // used with G = 8, measured faster there than one lane per row, while
+    // G = 2 and 4 on the 32-element level were slower):
+    // lane `sub` of a row's group takes the stencil terms sub, sub + G, ...,
+    // the group sums by shuffles and its first lane updates the row, so that a
+    // row's dependent chain is about S / G terms long and G times as many
+    // warps issue.  Warps whose rows all lie beyond the color skip; lanes past
+    // the last row repeat it (valid addresses) and store nothing.
+    template <bool VSH, int WHAT, int G>
+    __device__ __noinline__ void split_pass(const LevelDesc& L, const CTab& t, int c0, int c1, int c2, int cnt,
+                                            const T* __restrict__ vg, int vs, T* xl, const T* bl) const {
+        const int tid = threadIdx.x;
+        if ((tid & ~31) / G >= cnt) return;
+        const int blk = L.blk, xk0 = L.xk[0], xk01 = L.xk[0] * L.xk[1];
+        const int sub = tid & (G - 1);
+        const int qr = tid / G;
+        const bool act = qr < cnt;
+        const int q = act ? qr : cnt - 1;
+        const int t0 = q % t.k0, tr = q / t.k0;
+        const int t1 = tr % t.k1, t2 = tr / t.k1;
+        const int i0 = c0 + C0 * t0, i1 = c1 + C1 * t1, i2 = c2 + C2 * t2;
+        const bool msk = ieti_masked(mask, L.m, i0, i1, i2);
+        const int own = (t0 + 1) + xk0 * (t1 + 1) + (D == 3 ? xk01 * (t2 + 1) : 0);
+        const T* X = xl + own;
+        auto term = [&](int o) {
+            const int o0 = o % W0 - P0, o1 = (o / W0) % W1 - P1, o2 = o / (W0 * W1) - P2;
+            const int d0 = (c0 + o0 + C0) / C0 - 1, d1 = (c1 + o1 + C1) / C1 - 1;
+            int e = (o0 - C0 * d0) * blk + d0 + (o1 - C1 * d1) * C0 * blk + d1 * xk0;
+            if (D == 3) {
+                const int d2 = (c2 + o2 + C2) / C2 - 1;
+                e += (o2 - C2 * d2) * C0 * C1 * blk + d2 * xk01;
+            }
+            const T a = VSH ? shm<T>(vs)[q + o * cnt] : __ldg(vg + q + (long long)o * cnt);
+            return a * X[e];
+        };
+        constexpr int K = S / G;
+        T acc0 = T(0), acc1 = T(0);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            if (k & 1) acc1 += term(sub + k * G);
+            else acc0 += term(sub + k * G);
+        }
+        if (S % G != 0 && sub + K * G < S) acc0 += term(sub + K * G);
+        T acc = acc0 + acc1;
+#pragma unroll
+        for (int w = G / 2; w > 0; w >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, w);
+        if (sub == 0 && act) {
+            constexpr int oc = P0 + W0 * (P1 + W1 * P2);
+            if (WHAT == 0) {
+                if (!msk) {
+                    const T dg = VSH ? shm<T>(vs)[q + oc * cnt] : __ldg(vg + q + (long long)oc * cnt);
+                    xl[own] += (bl[q] - acc) / dg;
+                }
+            } else {
+                vp(r_off)[i0 + L.m[0] * (i1 + L.m[1] * i2)] = msk ? T(0) : bl[q] - acc;
+            }
+        }
+    }
+
     // sweep (WHAT = 0) or residual (WHAT = 1) over the rows of color c
     template <bool VSH, int WHAT>
     __device__ void color_pass(int l, int c) const {
@@ -268,7 +327,13 @@ struct VC {
         const int vs = ks_off + (int)(L.koff - kbase + vrel);
         T* xl = vp(x_off + L.xoff + c * blk);
         const T* bl = vp(b_off + L.boff + t.off);
-        for (int q = threadIdx.x; q < cnt; q += blockDim.x) {
+        const int nt = blockDim.x;
+        if (!(kflags & 256) && cnt > 0 && 8 * cnt <= nt) {
+            split_pass<VSH, WHAT, 8>(L, t, c0, c1, c2, cnt, vg, vs, xl, bl);
+            if (WHAT == 0) __syncthreads();
+            return;
+        }
+        for (int q = threadIdx.x; q < cnt; q += nt) {
             const int t0 = q % t.k0, tr = q / t.k0;
             const int t1 = tr % t.k1, t2 = tr / t.k1;
             const int i0 = c0 + C0 * t0, i1 = c1 + C1 * t1, i2 = c2 + C2 * t2;
