@@ -292,10 +292,11 @@ int ietidp_solve_batch_host(ietidp_handle* const* hs, int n, const double* const
                             double* const* u_host, ietidp_stats* stats);
 
 /* Autotuner decisions so far (process-wide): up to max_entries records of
- * 11 ints {dim, p0, p1, p2, kind (0 specialised, 1 global-memory vectors,
+ * 12 ints {dim, p0, p1, p2, kind (0 specialised, 1 global-memory vectors,
  * 2 run-time degree), mixed, waves, threads, smem bytes, CTAs per SM,
- * chosen variant keeps the V-cycle vectors in global memory} into out (may
- * be NULL); returns the number of decisions. */
+ * chosen variant keeps the V-cycle vectors in global memory, CTAs per slot
+ * (a thread-block cluster when > 1)} into out (may be NULL); returns the
+ * number of decisions. */
 int ietidp_autotune_table(int* out, int max_entries);
 
 /* Kernels launched so far in this process by the solve entry points

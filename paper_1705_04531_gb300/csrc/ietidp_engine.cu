@@ -46,9 +46,10 @@ struct TuneKey {
     int dim, p0, p1, p2, kind, mixed;   // kind: 0 specialised, 1 global-memory vectors, 2 run-time degree
     int waves;                          // ceil(slots / SMs)
     long long max_cost;                 // largest patch (rows x stencil)
+    int clok;                           // every launch of the stage may run as clusters
     bool operator<(const TuneKey& o) const {
-        return std::tie(dim, p0, p1, p2, kind, mixed, waves, max_cost) <
-               std::tie(o.dim, o.p0, o.p1, o.p2, o.kind, o.mixed, o.waves, o.max_cost);
+        return std::tie(dim, p0, p1, p2, kind, mixed, waves, max_cost, clok) <
+               std::tie(o.dim, o.p0, o.p1, o.p2, o.kind, o.mixed, o.waves, o.max_cost, o.clok);
     }
 };
 
@@ -57,7 +58,8 @@ struct TuneCfg {
     size_t smem;
     int ctas_per_sm;
     float ms;
-    int xg;   // V-cycle vectors in global memory (fewer bytes of shared memory per CTA)
+    int xg;      // V-cycle vectors in global memory (fewer bytes of shared memory per CTA)
+    int csize;   // CTAs per slot as one thread-block cluster (0 or 1: one CTA)
 };
 
 std::mutex g_tune_mu;
@@ -88,7 +90,8 @@ struct MGroup {
     size_t smem_min = 0;   // shared memory the kernel cannot do without (max)
     size_t tab_min = 0;    // color tables alone (minimum of the global-vector variant)
     int max_bw = 0;        // direct Neumann solves: largest half band width
-    TuneCfg cfg{512, 0, 1, 0.f, 0};
+    int clok = 0;          // the stage's modes all run as clusters (solve-phase modes)
+    TuneCfg cfg{512, 0, 1, 0.f, 0, 1};
 };
 
 }  // namespace
@@ -183,6 +186,7 @@ int ensure_side(ieti_engine* E, size_t n) {
 cudaError_t launch_cfg(const SolveArgs& a, const MGroup& g, const TuneCfg& c, cudaStream_t st) {
     SolveArgs b = a;
     b.smem_bytes = c.smem;
+    b.csize = c.csize;
     if (g.kind == 3) return launch_direct_neumann(b, g.max_bw, st);
     if (g.kind == 2) return launch_solve(b, c.threads, st);
     return launch_solve_variant(b, g.dim, g.p0, g.p1, g.p2, c.threads, st, g.kind == 1 || c.xg);
@@ -209,10 +213,19 @@ std::vector<TuneCfg> candidates(const MGroup& g) {
             if (b < lo) break;
             int occ = solve_variant_ctas_per_sm(g.dim, g.p0, g.p1, g.p2, g.mixed, gx, thr[k], b);
             if (occ >= want[k]) {
-                c.push_back(TuneCfg{thr[k], b, occ, 0.f, xg[k]});
+                c.push_back(TuneCfg{thr[k], b, occ, 0.f, xg[k], 1});
                 break;
             }
         }
+    }
+    // a thread-block cluster of 2, 4 or 8 CTAs per slot (global-vector
+    // variant, 512 threads, the full budget): several SMs on one patch, for
+    // launches with fewer slots than SMs (one problem at a time, or the
+    // largest patches of an uneven batch)
+    if (g.clok && (g.kind == 0 || g.kind == 1)) {
+        const size_t b = std::max(std::min(g.smem, (size_t)kSmemCap), g.tab_min);
+        for (int cs = 2; cs <= 8; cs *= 2)
+            if ((long long)g.s.size() * cs <= 2LL * sm_count()) c.push_back(TuneCfg{512, b, 1, 0.f, 1, cs});
     }
     return c;
 }
@@ -220,11 +233,11 @@ std::vector<TuneCfg> candidates(const MGroup& g) {
 // time each candidate on one V-cycle per slot (zero data, same work as a
 // real launch) and keep the fastest; cached per launch shape
 int tune(ieti_engine* E, MGroup& g, const std::vector<ietidp_handle*>& hs, long long* nlaunch) {
-    g.cfg = TuneCfg{512, g.smem, 1, 0.f, 0};
+    g.cfg = TuneCfg{512, g.smem, 1, 0.f, 0, 1};
     if (g.kind >= 2 || !autotune_enabled()) return IETIDP_OK;
     TuneKey key{g.dim, g.p0, g.p1, g.p2, g.kind, g.mixed,
                 (int)((g.s.size() + sm_count() - 1) / sm_count()),
-                *std::max_element(g.cost.begin(), g.cost.end())};
+                *std::max_element(g.cost.begin(), g.cost.end()), g.clok};
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune.find(key);
@@ -338,8 +351,23 @@ int merged_prepare(ieti_engine* E, std::vector<std::pair<ietidp_handle*, SolveAr
     }
     std::vector<ietidp_handle*> hs(items.size());
     for (size_t i = 0; i < items.size(); ++i) hs[i] = items[i].first;
+    // cluster launches serve the solve-phase modes only (the kernel refuses
+    // the others); IETIDP_CLUSTERS=0 keeps one CTA per slot, IETIDP_CLUSTERS=
+    // 2, 4 or 8 forces clusters of that size on every group that can take
+    // them (tests of the cluster path)
+    int clok = 1, cforce = 0;
+    {
+        const char* ce = std::getenv("IETIDP_CLUSTERS");
+        if (ce && ce[0] == '0') clok = 0;
+        if (ce && (ce[0] == '2' || ce[0] == '4' || ce[0] == '8')) cforce = ce[0] - '0';
+    }
+    for (const auto& it : items) {
+        const int md = it.second.mode;
+        if (!(md == MODE_NEUMANN || md == MODE_SCHUR || md == MODE_VCYCLE || md == MODE_VCYCLE_DIR)) clok = 0;
+    }
     for (auto& kv : by) {
         MGroup& m = kv.second;
+        m.clok = clok;
         // longest patches first, so that uneven batches finish together
         std::vector<size_t> ord(m.s.size());
         std::iota(ord.begin(), ord.end(), 0);
@@ -353,6 +381,8 @@ int merged_prepare(ieti_engine* E, std::vector<std::pair<ietidp_handle*, SolveAr
         m.s.swap(s2);
         m.cost.swap(c2);
         CHK(tune(E, m, hs, nlaunch));
+        if (cforce && clok && (m.kind == 0 || m.kind == 1))
+            m.cfg = TuneCfg{512, std::max(std::min(m.smem, (size_t)kSmemCap), m.tab_min), 1, 0.f, 1, cforce};
         MP.slots.insert(MP.slots.end(), m.s.begin(), m.s.end());
         MP.groups.push_back(std::move(m));
     }
@@ -1010,7 +1040,7 @@ extern "C" int ietidp_autotune_table(int* out, int max_entries) {
     int n = 0;
     for (const auto& kv : g_tune) {
         if (out && n < max_entries) {
-            int* o = out + 11 * n;
+            int* o = out + 12 * n;
             o[0] = kv.first.dim;
             o[1] = kv.first.p0;
             o[2] = kv.first.p1;
@@ -1022,6 +1052,7 @@ extern "C" int ietidp_autotune_table(int* out, int max_entries) {
             o[8] = (int)kv.second.smem;
             o[9] = kv.second.ctas_per_sm;
             o[10] = kv.first.kind == 1 || kv.second.xg;
+            o[11] = std::max(1, kv.second.csize);
         }
         ++n;
     }

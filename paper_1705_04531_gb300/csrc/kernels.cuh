@@ -187,6 +187,9 @@ struct SolveArgs {
     // natural order instead of the color-major ghost-padded layout, 256 one
     // lane per row in every color step (no lane groups on coarse levels)
     int kflags;
+    // launch shape (host side): CTAs per slot, as one thread-block cluster
+    // (global-vector variant, solve-phase modes); 0 or 1 = one CTA per slot
+    int csize;
 };
 
 // generic kernel (degrees known at run time only)

@@ -18,6 +18,7 @@
 // benchmarking.
 #pragma once
 #include <math.h>
+#include <cooperative_groups.h>
 #include "kernels.cuh"
 #include "sz_device.cuh"
 
@@ -80,6 +81,52 @@ __device__ __forceinline__ void cta_sum(double* val, Red& sh) {
         for (int i = 0; i < nw; ++i) s += sh.v[i][k];
         val[k] = s;
     }
+}
+
+// The CTAs that share one slot: a thread-block cluster of `size` CTAs (1
+// outside cluster launches).  Loops over a slot's rows and vector entries
+// run over the group's threads; group barriers are cluster barriers (release
+// / acquire: writes to global memory before the barrier are seen by every
+// CTA of the cluster after it).  Shared-memory copies (descriptor, tables,
+// staged matrices) stay per CTA.
+struct Grp {
+    int rank, size;
+    __device__ __forceinline__ int tid() const { return rank * (int)blockDim.x + (int)threadIdx.x; }
+    __device__ __forceinline__ int nt() const { return size * (int)blockDim.x; }
+    __device__ __forceinline__ void sync() const {
+        if (size > 1)
+            cooperative_groups::this_cluster().sync();
+        else
+            __syncthreads();
+    }
+};
+
+__device__ __forceinline__ Grp make_grp() {
+    Grp g;
+    g.rank = (int)cooperative_groups::this_cluster().block_rank();
+    g.size = (int)cooperative_groups::this_cluster().num_blocks();
+    return g;
+}
+
+// sums over the group: each CTA's total by cta_sum, then the CTAs' totals in
+// rank order (every CTA adds the same numbers in the same order, so all of
+// them take the same branches on the result)
+template <int K>
+__device__ __forceinline__ void grp_sum(double* val, Red& sh, double* tot, const Grp& g) {
+    cta_sum<K>(val, sh);
+    if (g.size == 1) return;
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k) tot[k] = val[k];
+    g.sync();
+    auto cl = cooperative_groups::this_cluster();
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        double s = 0.0;
+        for (int r = 0; r < g.size; ++r) s += *cl.map_shared_rank(tot + k, r);
+        val[k] = s;
+    }
+    g.sync();
 }
 
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
@@ -218,6 +265,7 @@ struct VC {
     const CTab* ct;       // [l * NC + c]
     long long* phase;     // phase timers (profiling builds)
     int kflags;           // SolveArgs::kflags
+    Grp g;                // the CTAs sharing the slot (a cluster, or this CTA)
 
     // one row of color (c0,c1,c2) at level l.  X: the row's own entry in x;
     // the neighbour at stencil offset (o0,o1,o2) lies e0(o0)+e1(o1)+e2(o2)
@@ -264,8 +312,8 @@ struct VC {
     // the last row repeat it (valid addresses) and store nothing.
     template <bool VSH, int WHAT, int G>
     __device__ __noinline__ void split_pass(const LevelDesc& L, const CTab& t, int c0, int c1, int c2, int cnt,
-                                            const T* __restrict__ vg, int vs, T* xl, const T* bl) const {
-        const int tid = threadIdx.x;
+                                               const T* __restrict__ vg, int vs, T* xl, const T* bl) const {
+        const int tid = g.tid();
         if ((tid & ~31) / G >= cnt) return;
         const int blk = L.blk, xk0 = L.xk[0], xk01 = L.xk[0] * L.xk[1];
         const int sub = tid & (G - 1);
@@ -327,13 +375,13 @@ struct VC {
         const int vs = ks_off + (int)(L.koff - kbase + vrel);
         T* xl = vp(x_off + L.xoff + c * blk);
         const T* bl = vp(b_off + L.boff + t.off);
-        const int nt = blockDim.x;
+        const int nt = g.nt();
         if (!(kflags & 256) && cnt > 0 && 8 * cnt <= nt) {
             split_pass<VSH, WHAT, 8>(L, t, c0, c1, c2, cnt, vg, vs, xl, bl);
-            if (WHAT == 0) __syncthreads();
+            if (WHAT == 0) g.sync();
             return;
         }
-        for (int q = threadIdx.x; q < cnt; q += nt) {
+        for (int q = g.tid(); q < cnt; q += nt) {
             const int t0 = q % t.k0, tr = q / t.k0;
             const int t1 = tr % t.k1, t2 = tr / t.k1;
             const int i0 = c0 + C0 * t0, i1 = c1 + C1 * t1, i2 = c2 + C2 * t2;
@@ -354,7 +402,7 @@ struct VC {
                 vp(r_off)[i] = rv;
             }
         }
-        if (WHAT == 0) __syncthreads();
+        if (WHAT == 0) g.sync();
     }
 
     // A level streamed from L2/HBM: its color blocks are moved into L2 by
@@ -380,12 +428,12 @@ struct VC {
             // the color after the sweep's last one is the first of the next
             // sweep (or, after forward sweeps, of the residual)
             auto col = [&](int k) { return forward ? k % NC : NC - 1 - k % NC; };
-            if (threadIdx.x == 0) {
+            if (g.tid() == 0) {
                 prefetch_block(l, col(0));
                 prefetch_block(l, col(1));
             }
             for (int cc = 0; cc < NC; ++cc) {
-                if (threadIdx.x == 0) prefetch_block(l, col(cc + 2));
+                if (g.tid() == 0) prefetch_block(l, col(cc + 2));
                 color_pass<false, 0>(l, col(cc));
             }
         }
@@ -396,11 +444,11 @@ struct VC {
             for (int c = 0; c < NC; ++c) color_pass<true, 1>(l, c);
         } else {
             for (int c = 0; c < NC; ++c) {
-                if (threadIdx.x == 0) prefetch_block(l, (c + 2) % NC);
+                if (g.tid() == 0) prefetch_block(l, (c + 2) % NC);
                 color_pass<false, 1>(l, c);
             }
         }
-        __syncthreads();
+        g.sync();
     }
 
     // color-major position of natural (i0,i1,i2) at level l >= 1
@@ -417,9 +465,9 @@ struct VC {
         T* xc = vp(x_off + Cl.xoff);
         const T* rs = vp(r_off);
         const int nxc = l - 1 >= 1 ? Cl.nx : Cl.n;
-        for (int t = threadIdx.x; t < nxc; t += blockDim.x) xc[t] = T(0);
+        for (int t = g.tid(); t < nxc; t += g.nt()) xc[t] = T(0);
         const int pp[3] = {P0, P1, P2};
-        for (int I = threadIdx.x; I < Cl.n; I += blockDim.x) {
+        for (int I = g.tid(); I < Cl.n; I += g.nt()) {
             const int I0 = I % Cl.m[0], Ir = I / Cl.m[0];
             const int I1 = Ir % Cl.m[1], I2 = Ir / Cl.m[1];
             const int dst = l - 1 >= 1 ? ieti_store_pos(Cl.m, pp, I0, I1, I2) : I;
@@ -456,7 +504,7 @@ struct VC {
             }
             bc[dst] = acc;
         }
-        __syncthreads();
+        g.sync();
     }
 
     // x_l += P x_{l-1}
@@ -466,7 +514,7 @@ struct VC {
         const T* xc = vp(x_off + Cl.xoff);
         T* x = vp(x_off + F.xoff);
         const bool cnat = l - 1 == 0;
-        for (int i = threadIdx.x; i < F.n; i += blockDim.x) {
+        for (int i = g.tid(); i < F.n; i += g.nt()) {
             const int i0 = i % F.m[0], ir = i / F.m[0];
             const int i1 = ir % F.m[1], i2 = ir / F.m[1];
             if (ieti_masked(mask, F.m, i0, i1, i2)) continue;
@@ -519,14 +567,14 @@ struct VC {
             }
             x[cm_pos(F, i0, i1, i2)] += acc;
         }
-        __syncthreads();
+        g.sync();
     }
 
     __device__ void coarsest() const {
         const int n = P->lev[0].n;
         const T* b = vp(b_off + P->lev[0].boff);
         T* x = vp(x_off + P->lev[0].xoff);
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        for (int i = g.tid(); i < n; i += g.nt()) {
             T acc0 = 0, acc1 = 0;
             int j = 0;
             if (a0_off >= 0) {
@@ -545,7 +593,7 @@ struct VC {
             }
             x[i] = acc0 + acc1;
         }
-        __syncthreads();
+        g.sync();
     }
 
     // x_fine = V(b_fine): b_fine (storage order, or natural for a 1-level
@@ -559,8 +607,8 @@ struct VC {
         {
             T* x = vp(x_off + P->lev[L - 1].xoff);
             const int nx = P->lev[L - 1].nx;
-            for (int i = threadIdx.x; i < nx; i += blockDim.x) x[i] = T(0);
-            __syncthreads();
+            for (int i = g.tid(); i < nx; i += g.nt()) x[i] = T(0);
+            g.sync();
         }
         for (int l = L - 1; l >= 1; --l) {
             {
@@ -629,7 +677,7 @@ struct VC {
 template <int D, int P0, int P1, int P2>
 __device__ __noinline__ void spmv64(const PatchDesc& P, const double* __restrict__ K64, const double* x, double* y,
                                     int rowmask, const double* sub, double scale, int only,
-                                    long long* phase = nullptr, int xs_off = -1) {
+                                    long long* phase = nullptr, int xs_off = -1, Grp g = Grp{0, 1}) {
     constexpr int W0 = 2 * P0 + 1, W1 = 2 * P1 + 1, W2 = 2 * P2 + 1, S = W0 * W1 * W2;
     constexpr int C0 = P0 + 1, C1 = P1 + 1, C2 = P2 + 1, NC = C0 * C1 * C2;
     const LevelDesc& F = P.lev[P.L - 1];
@@ -649,7 +697,7 @@ __device__ __noinline__ void spmv64(const PatchDesc& P, const double* __restrict
     for (int c = 0; c < C1; ++c) kk1[c] = ieti_cnt(m1, P1, c);
 #pragma unroll
     for (int c = 0; c < C2; ++c) kk2[c] = ieti_cnt(m2, P2, c);
-    for (int s = threadIdx.x; s < F.n; s += blockDim.x) {
+    for (int s = g.tid(); s < F.n; s += g.nt()) {
         int off = 0, c = 0, cnt = 0;
 #pragma unroll 1
         for (c = 0; c < NC; ++c) {
@@ -684,7 +732,7 @@ __device__ __noinline__ void spmv64(const PatchDesc& P, const double* __restrict
         if (sub) v = sub[i] + v;
         y[i] = v;
     }
-    __syncthreads();
+    g.sync();
     IETI_T1(49);
 }
 
@@ -888,20 +936,21 @@ __device__ void vcycle_apply(const VC<T, D, P0, P1, P2, XG>& vc, const double* r
     const int n = F.n;
     T* b = vc.vp(vc.b_off + F.boff);
     const int pp[3] = {P0, P1, P2};
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const Grp g = vc.g;
+    for (int i = g.tid(); i < n; i += g.nt()) {
         const int i0 = i % F.m[0], ir = i / F.m[0];
         const int i1 = ir % F.m[1], i2 = ir / F.m[1];
         b[L > 1 ? ieti_store_pos(F.m, pp, i0, i1, i2) : i] = (T)rin[i];
     }
-    __syncthreads();
+    g.sync();
     vc.run(nu1, nu2);
     const T* x = vc.vp(vc.x_off + F.xoff);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    for (int i = g.tid(); i < n; i += g.nt()) {
         const int i0 = i % F.m[0], ir = i / F.m[0];
         const int i1 = ir % F.m[1], i2 = ir / F.m[1];
         zout[i] = (double)x[L > 1 ? vc.cm_pos(F, i0, i1, i2) : i];
     }
-    __syncthreads();
+    g.sync();
 }
 
 __device__ inline void project_kerC(const SolveArgs& a, const PatchDesc& P, double* v, double* coef) {
@@ -930,14 +979,14 @@ __device__ inline void project_kerC(const SolveArgs& a, const PatchDesc& P, doub
     __syncthreads();
 }
 
-// v <- v - mean(v) over the n entries (one CTA)
-__device__ inline void remove_mean(double* v, int n, Red& red) {
+// v <- v - mean(v) over the n entries (the slot's group of CTAs)
+__device__ inline void remove_mean(double* v, int n, Red& red, double* tot, const Grp& g) {
     double s[1] = {0.0};
-    for (int i = threadIdx.x; i < n; i += blockDim.x) s[0] += v[i];
-    cta_sum<1>(s, red);
+    for (int i = g.tid(); i < n; i += g.nt()) s[0] += v[i];
+    grp_sum<1>(s, red, tot, g);
     const double mean = s[0] / n;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] -= mean;
-    __syncthreads();
+    for (int i = g.tid(); i < n; i += g.nt()) v[i] -= mean;
+    g.sync();
 }
 
 __device__ inline void apply_C(const SolveArgs& a, const PatchDesc& P, const double* v, double* coef) {
@@ -958,10 +1007,14 @@ __global__ void __launch_bounds__(512) k_solve_t(SolveArgs a0) {
     const IetiLaunchSpan span_(a0.tspan);
     __shared__ Red red;
     __shared__ double coef[kMaxRows];
+    __shared__ double gtot[4];
     __shared__ PatchDesc sP;
     __shared__ SolveArgs sa;
     unsigned char* dyn = ieti_dyn;
-    const SlotDesc sd = a0.slots[blockIdx.x];
+    // a cluster launch serves one slot per cluster (its CTAs split the rows;
+    // used for the modes of the solve phase on global-vector slots only)
+    const Grp grp = make_grp();
+    const SlotDesc sd = a0.slots[blockIdx.x / grp.size];
     if (threadIdx.x == 0) {
         sa = a0.batch ? a0.batch[sd.handle] : a0;
         sa.slots = a0.slots;
@@ -970,6 +1023,12 @@ __global__ void __launch_bounds__(512) k_solve_t(SolveArgs a0) {
     }
     __syncthreads();
     const SolveArgs& a = sa;
+    if (grp.size > 1 && (!XG || !(a.mode == MODE_NEUMANN || a.mode == MODE_SCHUR || a.mode == MODE_VCYCLE ||
+                                   a.mode == MODE_VCYCLE_DIR))) {
+        // not a cluster mode (every CTA of the cluster returns here)
+        if (grp.tid() == 0) atomicOr(a.flags, IETI_FLAG_BREAKDOWN);
+        return;
+    }
 #ifdef IETI_DEBUG_BOUNDS
     if (threadIdx.x == 0) g_ieti_dbg = a.dbg;
     __syncthreads();
@@ -1019,6 +1078,7 @@ __global__ void __launch_bounds__(512) k_solve_t(SolveArgs a0) {
         vc.A0g = A0g;
         vc.ct = (const CTab*)(dyn + pl.tab_off);
         vc.phase = a.phase;
+        vc.g = grp;
     }
     __syncthreads();
     vc.build_tables((CTab*)(dyn + pl.tab_off));
@@ -1050,7 +1110,7 @@ __global__ void __launch_bounds__(512) k_solve_t(SolveArgs a0) {
         else if (df)
             spmv_df<D, P0, P1, P2>(P, a.K32, a.K32lo, in, out, rmask, sb, sc, only, ph, xs_off);
         else
-            spmv64<D, P0, P1, P2>(P, a.K64, in, out, rmask, sb, sc, only, ph, xs_off);
+            spmv64<D, P0, P1, P2>(P, a.K64, in, out, rmask, sb, sc, only, ph, xs_off, grp);
     };
     if (a.mode == MODE_SCHUR) {
         const double* v = a.in + P.toff;
@@ -1061,15 +1121,15 @@ __global__ void __launch_bounds__(512) k_solve_t(SolveArgs a0) {
             } else {
                 opK(x, q, allsides, r, -1.0, 0, nullptr);
                 vcycle_apply(vc, q, z, a.nu1, a.nu2);
-                for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] += z[i];
-                __syncthreads();
+                for (int i = grp.tid(); i < n; i += grp.nt()) x[i] += z[i];
+                grp.sync();
             }
             ++vcount;
         }
-        for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = v[i] + x[i];
-        __syncthreads();
+        for (int i = grp.tid(); i < n; i += grp.nt()) p[i] = v[i] + x[i];
+        grp.sync();
         opK(p, a.out + P.toff, 0, nullptr, 1.0, 1, nullptr);
-        if (threadIdx.x == 0 && a.vstats) {
+        if (grp.tid() == 0 && a.vstats) {
             atomicAdd((unsigned long long*)&a.vstats[0], (unsigned long long)vcount);
             atomicAdd((unsigned long long*)&a.vstats[1], (unsigned long long)(vcount * n));
         }
@@ -1082,18 +1142,18 @@ __global__ void __launch_bounds__(512) k_solve_t(SolveArgs a0) {
         const int rmask = kind == 0 ? P.dmask : allsides;
         for (int c = 0; c < a.ncycles; ++c) {
             opK(xx, r, rmask, bb, -1.0, 0, a.phase);
-            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            for (int i = grp.tid(); i < n; i += grp.nt()) {
                 const int i0 = i % F.m[0], ir = i / F.m[0];
                 const int i1 = ir % F.m[1], i2 = ir / F.m[1];
                 if (ieti_masked(rmask, F.m, i0, i1, i2)) r[i] = 0.0;
             }
-            __syncthreads();
+            grp.sync();
             vcycle_apply(vc, r, z, a.nu1, a.nu2);
-            for (int i = threadIdx.x; i < n; i += blockDim.x) xx[i] += z[i];
-            __syncthreads();
+            for (int i = grp.tid(); i < n; i += grp.nt()) xx[i] += z[i];
+            grp.sync();
             ++vcount;
         }
-        if (threadIdx.x == 0 && a.vstats) {
+        if (grp.tid() == 0 && a.vstats) {
             atomicAdd((unsigned long long*)&a.vstats[0], (unsigned long long)vcount);
             atomicAdd((unsigned long long*)&a.vstats[1], (unsigned long long)(vcount * n));
         }
@@ -1235,37 +1295,30 @@ __global__ void __launch_bounds__(512) k_solve_t(SolveArgs a0) {
         project_kerC(a, P, r, coef);
     } else {
         const double* g = a.in + P.toff;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        for (int i = grp.tid(); i < n; i += grp.nt()) {
             const int i0 = i % F.m[0], ir = i / F.m[0];
             const int i1 = ir % F.m[1], i2 = ir / F.m[1];
             r[i] = ieti_masked(P.dmask, F.m, i0, i1, i2) ? 0.0 : g[i];
             x[i] = 0.0;
         }
-        __syncthreads();
+        grp.sync();
         // b = P^T g = g - C^T (Phi^T g)
         {
-            const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+            const int lane = threadIdx.x & 31, w = grp.tid() >> 5, nw = grp.nt() >> 5;
             for (int j = w; j < P.npi; j += nw) {
                 const int row = P.crow0 + j;
                 const double cj = a.rpi_loc[row];
                 for (int e = a.crow_ptr[row] + lane; e < a.crow_ptr[row + 1]; e += 32) r[a.c_idx[e]] -= a.c_w[e] * cj;
             }
         }
-        __syncthreads();
-        if (P.floating) {
-            double s[1] = {0.0};
-            for (int i = threadIdx.x; i < n; i += blockDim.x) s[0] += r[i];
-            cta_sum<1>(s, red);
-            const double mean = s[0] / n;
-            for (int i = threadIdx.x; i < n; i += blockDim.x) r[i] -= mean;
-            __syncthreads();
-        }
+        grp.sync();
+        if (P.floating) remove_mean(r, n, red, gtot, grp);
     }
     double nb2;
     {
         double s[1] = {0.0};
-        for (int i = threadIdx.x; i < n; i += blockDim.x) s[0] += r[i] * r[i];
-        cta_sum<1>(s, red);
+        for (int i = grp.tid(); i < n; i += grp.nt()) s[0] += r[i] * r[i];
+        grp_sum<1>(s, red, gtot, grp);
         nb2 = s[0];
     }
     int it = 0;
@@ -1278,15 +1331,15 @@ __global__ void __launch_bounds__(512) k_solve_t(SolveArgs a0) {
         vcycle_apply(vc, r, z, a.nu1, a.nu2);
         ++vcount;
         if (basis) project_kerC(a, P, z, coef);
-        if (proj1) remove_mean(z, n, red);
+        if (proj1) remove_mean(z, n, red, gtot, grp);
         double rz;
         {
             double s[1] = {0.0};
-            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            for (int i = grp.tid(); i < n; i += grp.nt()) {
                 p[i] = z[i];
                 s[0] += r[i] * z[i];
             }
-            cta_sum<1>(s, red);
+            grp_sum<1>(s, red, gtot, grp);
             rz = s[0];
         }
         for (it = 1; it <= a.maxit; ++it) {
@@ -1296,22 +1349,22 @@ __global__ void __launch_bounds__(512) k_solve_t(SolveArgs a0) {
             else
                 opK(p, q, P.dmask, nullptr, 1.0, 0, a.phase);
             if (basis) project_kerC(a, P, q, coef);
-            for (int i = threadIdx.x; i < n; i += blockDim.x) s[0] += p[i] * q[i];
-            cta_sum<1>(s, red);
+            for (int i = grp.tid(); i < n; i += grp.nt()) s[0] += p[i] * q[i];
+            grp_sum<1>(s, red, gtot, grp);
             const double pq = s[0];
             if (!(pq > 0.0) || !isfinite(pq)) {
-                if (threadIdx.x == 0) atomicOr(a.flags, IETI_FLAG_BREAKDOWN);
+                if (grp.tid() == 0) atomicOr(a.flags, IETI_FLAG_BREAKDOWN);
                 break;
             }
             const double alpha = rz / pq;
             double s2[1] = {0.0};
-            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            for (int i = grp.tid(); i < n; i += grp.nt()) {
                 x[i] += alpha * p[i];
                 const double ri = r[i] - alpha * q[i];
                 r[i] = ri;
                 s2[0] += ri * ri;
             }
-            cta_sum<1>(s2, red);
+            grp_sum<1>(s2, red, gtot, grp);
             if (s2[0] <= tol2) {
                 conv = true;
                 break;
@@ -1319,21 +1372,21 @@ __global__ void __launch_bounds__(512) k_solve_t(SolveArgs a0) {
             vcycle_apply(vc, r, z, a.nu1, a.nu2);
             ++vcount;
             if (basis) project_kerC(a, P, z, coef);
-            if (proj1) remove_mean(z, n, red);
+            if (proj1) remove_mean(z, n, red, gtot, grp);
             double s3[2] = {0.0, 0.0};
-            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            for (int i = grp.tid(); i < n; i += grp.nt()) {
                 s3[0] += r[i] * z[i];
                 s3[1] += q[i] * z[i];
             }
-            cta_sum<2>(s3, red);
+            grp_sum<2>(s3, red, gtot, grp);
             const double beta = a.mixed ? -alpha * s3[1] / rz : s3[0] / rz;
             rz = s3[0];
-            for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = z[i] + beta * p[i];
-            __syncthreads();
+            for (int i = grp.tid(); i < n; i += grp.nt()) p[i] = z[i] + beta * p[i];
+            grp.sync();
         }
         if (!conv && it > a.maxit) it = a.maxit;
     }
-    if (threadIdx.x == 0) {
+    if (grp.tid() == 0) {
         a.its[sd.its] = it;
         if (!conv) atomicOr(a.flags, IETI_FLAG_NOT_CONVERGED);
         if (a.vstats) {
@@ -1348,12 +1401,14 @@ __global__ void __launch_bounds__(512) k_solve_t(SolveArgs a0) {
         for (int i = threadIdx.x; i < n; i += blockDim.x) phicol[i] += x[i];
         return;
     }
+    // every CTA of the group forms the coefficients (x is complete after the
+    // group barrier that ended the CG) in its own shared memory
     apply_C(a, P, x, coef);
     for (int j = threadIdx.x; j < P.npi; j += blockDim.x) coef[j] -= a.upi_loc[P.crow0 + j];
     __syncthreads();
     double* out = a.out + P.toff;
     const double* ph = a.phi + P.phioff;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    for (int i = grp.tid(); i < n; i += grp.nt()) {
         double u = x[i];
         for (int j = 0; j < P.npi; ++j) u -= coef[j] * ph[(long long)j * n + i];
         out[i] = u;
@@ -1372,6 +1427,24 @@ cudaError_t launch_t(const SolveArgs& a, int threads, cudaStream_t st, int* occ)
     if (e != cudaSuccess) return e;
     if (occ) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, kern, threads, a.smem_bytes);
     if (a.nslots == 0) return cudaSuccess;
+    if (a.csize > 1) {
+        // one cluster of csize CTAs per slot (a shape whose cluster does not
+        // fit on the GPU is refused by the launch: an error, nothing runs)
+        if (!XG || a.csize > 8) return cudaErrorInvalidConfiguration;
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = (unsigned)a.csize;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3((unsigned)(a.nslots * a.csize));
+        cfg.blockDim = dim3((unsigned)threads);
+        cfg.dynamicSmemBytes = a.smem_bytes;
+        cfg.stream = st;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, kern, a);
+    }
     kern<<<a.nslots, threads, a.smem_bytes, st>>>(a);
     return cudaGetLastError();
 }

@@ -300,10 +300,11 @@ def kernel_launches():
 def autotune_table():
     """Autotuner decisions: list of dicts (shape key and chosen configuration)."""
     n = _lib.ietidp_autotune_table(None, 0)
-    buf = (C.c_int * (11 * max(n, 1)))()
+    buf = (C.c_int * (12 * max(n, 1)))()
     n = _lib.ietidp_autotune_table(buf, n)
-    keys = ("dim", "p0", "p1", "p2", "kind", "mixed", "waves", "threads", "smem", "ctas_per_sm", "global_vectors")
-    return [dict(zip(keys, buf[11 * i:11 * i + 11])) for i in range(n)]
+    keys = ("dim", "p0", "p1", "p2", "kind", "mixed", "waves", "threads", "smem", "ctas_per_sm", "global_vectors",
+            "cluster")
+    return [dict(zip(keys, buf[12 * i:12 * i + 12])) for i in range(n)]
 
 
 class Problem:

@@ -61,6 +61,9 @@ DOMS = {
     "annulus3x3_p5_floating": lambda: W.annulus_6x6(8, 5, grid=(3, 3)),
     "uneven_p5_p7": lambda: W.random_quad_rhs(_uneven(), seed=5),
     "cube_p4": lambda: W.random_quad_rhs(W.cube_2x2x2(4, 4), seed=7),
+    # curved patches on which the high-order V-cycle overshoots (eigenvalues
+    # of V K above 1): the primal basis must come from the standard hierarchy
+    "annulus3x3_p4_n16": lambda: W.annulus_6x6(16, 4, grid=(3, 3)),
 }
 
 _ORC = {}
