@@ -89,32 +89,42 @@ __device__ __forceinline__ void cta_sum(double* val, Red& sh) {
 // / acquire: writes to global memory before the barrier are seen by every
 // CTA of the cluster after it).  Shared-memory copies (descriptor, tables,
 // staged matrices) stay per CTA.
-struct Grp {
+// CL = false (the shared-vector variant, never launched as clusters): one
+// CTA, resolved at compile time.
+template <bool CL>
+struct GrpT {
     int rank, size;
-    __device__ __forceinline__ int tid() const { return rank * (int)blockDim.x + (int)threadIdx.x; }
-    __device__ __forceinline__ int nt() const { return size * (int)blockDim.x; }
+    __device__ __forceinline__ int tid() const {
+        return CL ? rank * (int)blockDim.x + (int)threadIdx.x : (int)threadIdx.x;
+    }
+    __device__ __forceinline__ int nt() const { return CL ? size * (int)blockDim.x : (int)blockDim.x; }
+    __device__ __forceinline__ bool many() const { return CL && size > 1; }
     __device__ __forceinline__ void sync() const {
-        if (size > 1)
+        if (many())
             cooperative_groups::this_cluster().sync();
         else
             __syncthreads();
     }
 };
+using Grp = GrpT<true>;
 
-__device__ __forceinline__ Grp make_grp() {
-    Grp g;
-    g.rank = (int)cooperative_groups::this_cluster().block_rank();
-    g.size = (int)cooperative_groups::this_cluster().num_blocks();
+template <bool CL>
+__device__ __forceinline__ GrpT<CL> make_grp() {
+    GrpT<CL> g{0, 1};
+    if (CL) {
+        g.rank = (int)cooperative_groups::this_cluster().block_rank();
+        g.size = (int)cooperative_groups::this_cluster().num_blocks();
+    }
     return g;
 }
 
 // sums over the group: each CTA's total by cta_sum, then the CTAs' totals in
 // rank order (every CTA adds the same numbers in the same order, so all of
 // them take the same branches on the result)
-template <int K>
-__device__ __forceinline__ void grp_sum(double* val, Red& sh, double* tot, const Grp& g) {
+template <int K, bool CL>
+__device__ __forceinline__ void grp_sum(double* val, Red& sh, double* tot, const GrpT<CL>& g) {
     cta_sum<K>(val, sh);
-    if (g.size == 1) return;
+    if (!g.many()) return;
     if (threadIdx.x == 0)
 #pragma unroll
         for (int k = 0; k < K; ++k) tot[k] = val[k];
@@ -265,7 +275,7 @@ struct VC {
     const CTab* ct;       // [l * NC + c]
     long long* phase;     // phase timers (profiling builds)
     int kflags;           // SolveArgs::kflags
-    Grp g;                // the CTAs sharing the slot (a cluster, or this CTA)
+    GrpT<XG> g;           // the CTAs sharing the slot (a cluster, or this CTA)
 
     // one row of color (c0,c1,c2) at level l.  X: the row's own entry in x;
     // the neighbour at stencil offset (o0,o1,o2) lies e0(o0)+e1(o1)+e2(o2)
@@ -674,10 +684,10 @@ struct VC {
 // offset (doubles; a free region of at least n doubles), so that a row's
 // neighbour reads are shared-memory loads and its registers hold only the
 // streamed matrix values.
-template <int D, int P0, int P1, int P2>
+template <int D, int P0, int P1, int P2, bool CL = false>
 __device__ __noinline__ void spmv64(const PatchDesc& P, const double* __restrict__ K64, const double* x, double* y,
                                     int rowmask, const double* sub, double scale, int only,
-                                    long long* phase = nullptr, int xs_off = -1, Grp g = Grp{0, 1}) {
+                                    long long* phase = nullptr, int xs_off = -1, GrpT<CL> g = GrpT<CL>{0, 1}) {
     constexpr int W0 = 2 * P0 + 1, W1 = 2 * P1 + 1, W2 = 2 * P2 + 1, S = W0 * W1 * W2;
     constexpr int C0 = P0 + 1, C1 = P1 + 1, C2 = P2 + 1, NC = C0 * C1 * C2;
     const LevelDesc& F = P.lev[P.L - 1];
@@ -936,7 +946,7 @@ __device__ void vcycle_apply(const VC<T, D, P0, P1, P2, XG>& vc, const double* r
     const int n = F.n;
     T* b = vc.vp(vc.b_off + F.boff);
     const int pp[3] = {P0, P1, P2};
-    const Grp g = vc.g;
+    const GrpT<XG> g = vc.g;
     for (int i = g.tid(); i < n; i += g.nt()) {
         const int i0 = i % F.m[0], ir = i / F.m[0];
         const int i1 = ir % F.m[1], i2 = ir / F.m[1];
@@ -980,7 +990,8 @@ __device__ inline void project_kerC(const SolveArgs& a, const PatchDesc& P, doub
 }
 
 // v <- v - mean(v) over the n entries (the slot's group of CTAs)
-__device__ inline void remove_mean(double* v, int n, Red& red, double* tot, const Grp& g) {
+template <bool CL>
+__device__ inline void remove_mean(double* v, int n, Red& red, double* tot, const GrpT<CL>& g) {
     double s[1] = {0.0};
     for (int i = g.tid(); i < n; i += g.nt()) s[0] += v[i];
     grp_sum<1>(s, red, tot, g);
@@ -1013,7 +1024,7 @@ __global__ void __launch_bounds__(512) k_solve_t(SolveArgs a0) {
     unsigned char* dyn = ieti_dyn;
     // a cluster launch serves one slot per cluster (its CTAs split the rows;
     // used for the modes of the solve phase on global-vector slots only)
-    const Grp grp = make_grp();
+    const GrpT<XG> grp = make_grp<XG>();
     const SlotDesc sd = a0.slots[blockIdx.x / grp.size];
     if (threadIdx.x == 0) {
         sa = a0.batch ? a0.batch[sd.handle] : a0;
@@ -1110,7 +1121,7 @@ __global__ void __launch_bounds__(512) k_solve_t(SolveArgs a0) {
         else if (df)
             spmv_df<D, P0, P1, P2>(P, a.K32, a.K32lo, in, out, rmask, sb, sc, only, ph, xs_off);
         else
-            spmv64<D, P0, P1, P2>(P, a.K64, in, out, rmask, sb, sc, only, ph, xs_off, grp);
+            spmv64<D, P0, P1, P2, XG>(P, a.K64, in, out, rmask, sb, sc, only, ph, xs_off, grp);
     };
     if (a.mode == MODE_SCHUR) {
         const double* v = a.in + P.toff;
