@@ -351,6 +351,21 @@ int ietidp_vcycles_hierarchy(ietidp_handle* h, int hierarchy, const double* b, d
  * ietidp_vcycles. */
 int ietidp_vcycles_noalloc(ietidp_handle* h, const double* b, double* x, int ncycles);
 
+/* Operators of the high-order multigrid (Sec. 4) of one patch, built on the
+ * host in FP64 with no device work (inspection and tests).  Hierarchy `kind`
+ * 0 (Neumann: the sides in dmask removed; alpha M^ added when dmask == 0) or
+ * 1 (Dirichlet: every side removed).  Out, host: sizes[0..2] the free fine
+ * functions per direction, sizes[3..5] the free degree-1 functions on half
+ * the elements (1 beyond dim); U the smoother's generalized eigenvectors per
+ * direction, U_r[j + nf_r i], directions one after the other; P the L2
+ * prolongations, P_r[j + nf_r c], likewise; Dinv 1 / (sum_r c_r lambda_r
+ * + alpha c_M) on the nf_0 x nf_1 (x nf_2) grid, first direction fastest.
+ * U, P, Dinv may be NULL (sizes only).  IETIDP_E_INVALID_ARG for a bad
+ * dimension, degree (1..7), element count, kind or a 3D patch that is not a
+ * box. */
+int ietidp_ho_patch_operators(int dim, const iga_patch_desc* patch, unsigned dmask, double alpha, int kind,
+                              int* sizes, double* U, double* P, double* Dinv);
+
 /* Helpers exposed for testing the building blocks against the oracle:
  *  - ietidp_apply_K: y = K x per patch (Dirichlet rows/cols removed);
  *  - ietidp_apply_F: q = F p on the multipliers (device, n_lambda);

@@ -542,3 +542,40 @@ int ieti_ho_build(const iga_problem* Pb, const std::vector<PatchDesc>& pd, doubl
     }
     return IETIDP_OK;
 }
+
+// one patch's operators on the host, for inspection and tests (no device work)
+extern "C" int ietidp_ho_patch_operators(int dim, const iga_patch_desc* patch, unsigned dmask, double alpha,
+                                         int kind, int* sizes, double* U, double* P, double* Dinv) {
+    if (!patch || !sizes || (dim != 2 && dim != 3) || (kind != 0 && kind != 1) || alpha < 0)
+        return fail(IETIDP_E_INVALID_ARG, "bad argument");
+    for (int r = 0; r < dim; ++r)
+        if (patch->degree[r] < 1 || patch->degree[r] > IETI_MAXP - 1 || patch->nelem[r] < 1)
+            return fail(IETIDP_E_INVALID_ARG, "bad degree or element count");
+    iga_problem Pb;
+    Pb.dim = dim;
+    Pb.npatch = 1;
+    Pb.patches.assign(1, *patch);
+    Pb.dmask.assign(1, (int)dmask);
+    std::vector<PatchDesc> pd(1);
+    std::memset(pd.data(), 0, sizeof(PatchDesc));
+    std::vector<HoDesc> desc;
+    std::vector<double> pool;
+    const int rc = ieti_ho_build(&Pb, pd, alpha, desc, pool);
+    if (rc != IETIDP_OK) return rc;
+    const HoDesc& H = desc[0];
+    long long nu = 0, np = 0, nd = 1;
+    for (int r = 0; r < 3; ++r) {
+        sizes[r] = H.nf[kind][r];
+        sizes[3 + r] = H.nc[kind][r];
+        nd *= H.nf[kind][r];
+    }
+    for (int r = 0; r < dim; ++r) {
+        const long long nf = H.nf[kind][r], nc = H.nc[kind][r];
+        if (U) std::copy(pool.begin() + H.u[kind][r], pool.begin() + H.u[kind][r] + nf * nf, U + nu);
+        if (P) std::copy(pool.begin() + H.pt[kind][r], pool.begin() + H.pt[kind][r] + nf * nc, P + np);
+        nu += nf * nf;
+        np += nf * nc;
+    }
+    if (Dinv) std::copy(pool.begin() + H.dinv[kind], pool.begin() + H.dinv[kind] + nd, Dinv);
+    return IETIDP_OK;
+}

@@ -125,6 +125,8 @@ _SIGS = {
     "ietidp_server_status": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_longlong), C.POINTER(C.c_int)]),
     "ietidp_server_estimate": (C.c_longlong, [_vp, C.POINTER(iga_domain_desc)]),
     "ietidp_server_destroy": (C.c_int, [_vp]),
+    "ietidp_ho_patch_operators": (C.c_int, [C.c_int, C.POINTER(iga_patch_desc), C.c_uint, C.c_double, C.c_int,
+                                            C.POINTER(C.c_int), _vp, _vp, _vp]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -240,6 +242,32 @@ def iga_topology(desc):
     _check(_lib.iga_topology(C.byref(desc), C.byref(info), dm))
     out = {f: getattr(info, f) for f, _ in iga_topology_info._fields_}
     return out, [int(dm[k]) for k in range(desc.npatch)]
+
+
+def ho_patch_operators(dom: W.Domain, k: int, kind: int, alpha: float = 1e-2):
+    """High-order multigrid operators of patch k (host, FP64, no device work):
+    (U_r list, P_r list, Dinv) with U_r[j, i] = eigenvector i at function j,
+    P_r[j, c], Dinv on the free grid (first direction fastest)."""
+    desc, keep = domain_desc(dom)
+    _, dmask = iga_topology(desc)
+    d = dom.dim
+    sz = (C.c_int * 6)()
+    pat = desc.patches[k]
+    _check(_lib.ietidp_ho_patch_operators(d, C.byref(pat), dmask[k], alpha, kind, sz, None, None, None))
+    nf, nc = list(sz[:3]), list(sz[3:])
+    U = np.zeros(sum(nf[r] * nf[r] for r in range(d)))
+    P = np.zeros(sum(nf[r] * nc[r] for r in range(d)))
+    Dinv = np.zeros(int(np.prod(nf)))
+    _check(_lib.ietidp_ho_patch_operators(d, C.byref(pat), dmask[k], alpha, kind, sz,
+                                          U.ctypes.data_as(C.c_void_p), P.ctypes.data_as(C.c_void_p),
+                                          Dinv.ctypes.data_as(C.c_void_p)))
+    Us, Ps, ou, op = [], [], 0, 0
+    for r in range(d):
+        Us.append(U[ou:ou + nf[r] * nf[r]].reshape(nf[r], nf[r]).T.copy())   # [j, i]
+        Ps.append(P[op:op + nf[r] * nc[r]].reshape(nc[r], nf[r]).T.copy())   # [j, c]
+        ou += nf[r] * nf[r]
+        op += nf[r] * nc[r]
+    return Us, Ps, Dinv
 
 
 def iga_assemble_patches(dom: W.Domain, stream=None):
