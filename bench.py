@@ -65,6 +65,8 @@ def parse():
                          "phases: per-phase times of a batched V-cycle (library built with "
                          "IETIDP_PHASE_TIMERS=1)")
     ap.add_argument("--sm-mhz", type=float, default=2070.0, help="phases: SM clock for cycle counts")
+    ap.add_argument("--mg-kind", default="standard", choices=["standard", "highorder"],
+                    help="phases: multigrid of the solvers")
     ap.add_argument("--rate", type=float, default=None, help="serve: arrivals per second (one rate)")
     ap.add_argument("--nreq", type=int, default=512, help="serve: requests in the stream")
     ap.add_argument("--concurrency", type=int, default=8, help="serve: worker streams")
@@ -598,7 +600,7 @@ def run_phases(args):
     from paper_1705_04531_gb300 import ietidp as api
     dom = workload(args.workload)
     probs = [api.Problem(dom) for _ in range(args.batch)]
-    sols = [api.Solver(p_, precision=args.precision) for p_ in probs]
+    sols = [api.Solver(p_, precision=args.precision, mg_kind=args.mg_kind) for p_ in probs]
     api.Solver.solve_batch(sols)        # autotuning of the merged launches
     fs = [p_.load() for p_ in probs]
     xs = [torch.zeros_like(f) for f in fs]
@@ -608,12 +610,14 @@ def run_phases(args):
     ms = [api.Solver.vcycles_batch(sols, fs, xs, 1) for _ in range(10)]
     q1 = sols[0].phase_timers()
     dq = (q1 - q0) / 10 / args.sm_mhz
-    names = {48: "coarsest", 49: "fine_operator"}
+    names = {48: "coarsest", 49: "fine_operator", 52: "ho_fine_residuals", 53: "ho_smoother",
+             54: "ho_restriction", 55: "ho_degree1_vcycle", 56: "ho_prolongation",
+             57: "generic_fine_operator", 58: "generic_conversions"}
     for l in range(1, 12):
         for k, nm in enumerate(["sweeps", "residual", "restrict", "prolong"]):
             names[4 * l + k] = f"level{l}_{nm}"
     print(json.dumps({"mode": "phases", "workload": args.workload, "batch": args.batch,
-                      "precision": args.precision, "launch_ms": float(np.median(ms)),
+                      "precision": args.precision, "mg_kind": args.mg_kind, "launch_ms": float(np.median(ms)),
                       "phase_us": {names[i]: round(float(dq[i]), 1) for i in sorted(names) if dq[i] != 0}}))
 
 

@@ -49,16 +49,19 @@ struct Tabs {
 // (A x)_i for one row: banded stiffness of a level plus, when alpha != 0,
 // alpha times the Kronecker parameter mass.  Returns the diagonal in *diag.
 // vals: the color block of the row's color (offset-major), cnt its rows,
-// s the row's number q inside the color
-template <typename V, typename X, typename A>
-__device__ __forceinline__ A row_apply(const V* __restrict__ vals, int cnt, int s, const X* x,
-                                       const int* m, const int* p, int i0, int i1, int i2,
-                                       const V* mt0, const V* mt1, const V* mt2, A alpha, A* diag) {
+// s the row's number q inside the color.  Each line of the stencil (fixed
+// o1, o2) is read into registers first, WM entries at most (WM >= 2 p0 + 1,
+// entries past the line's end predicated off), so that its loads are in
+// flight together, and summed into four partial sums.
+template <int WM, typename V, typename X, typename A>
+__device__ __forceinline__ A row_apply_w(const V* __restrict__ vals, int cnt, int s, const X* x,
+                                         const int* m, const int* p, int i0, int i1, int i2,
+                                         const V* mt0, const V* mt1, const V* mt2, A alpha, A* diag) {
     int lo0 = max(-p[0], -i0), hi0 = min(p[0], m[0] - 1 - i0);
     int lo1 = max(-p[1], -i1), hi1 = min(p[1], m[1] - 1 - i1);
     int lo2 = max(-p[2], -i2), hi2 = min(p[2], m[2] - 1 - i2);
     int w0 = 2 * p[0] + 1, w1 = 2 * p[1] + 1;
-    A acc = 0;
+    A acc[4] = {A(0), A(0), A(0), A(0)};
     for (int o2 = lo2; o2 <= hi2; ++o2)
         for (int o1 = lo1; o1 <= hi1; ++o1) {
             int ob = ((o2 + p[2]) * w1 + (o1 + p[1])) * w0 + p[0];
@@ -68,11 +71,23 @@ __device__ __forceinline__ A row_apply(const V* __restrict__ vals, int cnt, int 
                 m12 = (A)mt1[i1 * w1 + o1 + p[1]];
                 if (mt2) m12 *= (A)mt2[i2 * (2 * p[2] + 1) + o2 + p[2]];
             }
-            for (int o0 = lo0; o0 <= hi0; ++o0) {
-                A v = (A)vals[(long long)(ob + o0) * cnt + s];
-                if (alpha != A(0)) v += alpha * (A)mt0[i0 * w0 + o0 + p[0]] * m12;
-                acc += v * (A)x[xb + o0];
+            A vv[WM], xv[WM];
+#pragma unroll
+            for (int k = 0; k < WM; ++k) {
+                const int o0 = lo0 + k;
+                const bool ok = o0 <= hi0;
+                vv[k] = ok ? (A)vals[(long long)(ob + o0) * cnt + s] : A(0);
+                xv[k] = ok ? (A)x[xb + o0] : A(0);
             }
+            if (alpha != A(0)) {
+#pragma unroll
+                for (int k = 0; k < WM; ++k) {
+                    const int o0 = lo0 + k;
+                    if (o0 <= hi0) vv[k] += alpha * (A)mt0[i0 * w0 + o0 + p[0]] * m12;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < WM; ++k) acc[k & 3] += vv[k] * xv[k];
         }
     if (diag) {
         int oc = ((p[2]) * w1 + p[1]) * w0 + p[0];
@@ -84,8 +99,35 @@ __device__ __forceinline__ A row_apply(const V* __restrict__ vals, int cnt, int 
         }
         *diag = d;
     }
-    return acc;
+    return (acc[0] + acc[1]) + (acc[2] + acc[3]);
 }
+
+template <typename V, typename X, typename A>
+__device__ __forceinline__ A row_apply(const V* __restrict__ vals, int cnt, int s, const X* x,
+                                       const int* m, const int* p, int i0, int i1, int i2,
+                                       const V* mt0, const V* mt1, const V* mt2, A alpha, A* diag) {
+    if (p[0] <= 1)
+        return row_apply_w<3, V, X, A>(vals, cnt, s, x, m, p, i0, i1, i2, mt0, mt1, mt2, alpha, diag);
+    if (p[0] <= 3)
+        return row_apply_w<7, V, X, A>(vals, cnt, s, x, m, p, i0, i1, i2, mt0, mt1, mt2, alpha, diag);
+    return row_apply_w<2 * (IETI_MAXP - 1) + 1, V, X, A>(vals, cnt, s, x, m, p, i0, i1, i2, mt0, mt1, mt2, alpha,
+                                                         diag);
+}
+
+// Optional phase counters (built with -DIETI_PHASE_TIMERS): thread 0 of CTA 0
+// adds clock cycles per phase to phase[]: [52] fine residuals of the
+// high-order V-cycle, [53] its smoother, [54] restriction, [55] degree-1
+// V-cycle, [56] prolongation, [57] the CG's fine operator (V-cycle mode:
+// the residual), [58] V-cycle input / output conversions.
+#ifdef IETI_PHASE_TIMERS
+#define HO_DECL() long long _h0 = 0
+#define HO_T0() do { if (threadIdx.x == 0 && blockIdx.x == 0) _h0 = clock64(); } while (0)
+#define HO_T1(ph, k) do { if (threadIdx.x == 0 && blockIdx.x == 0 && (ph)) (ph)[k] += clock64() - _h0; } while (0)
+#else
+#define HO_DECL() do {} while (0)
+#define HO_T0() do {} while (0)
+#define HO_T1(ph, k) do {} while (0)
+#endif
 
 template <typename T>
 struct VCycle {
@@ -108,6 +150,7 @@ struct VCycle {
     const VCycle<T>* coarse = nullptr;
     T* t1 = nullptr;
     T* t2 = nullptr;
+    long long* phase = nullptr;   // phase counters (profiling builds)
 
     __device__ T* X(int l) const { return lvec + P->lev[l].voff; }
     __device__ T* B(int l) const { return lvec + nlvec + P->lev[l].voff; }
@@ -401,6 +444,7 @@ __device__ void ho_smooth(const VCycle<T>& vc) {
 // to the degree-1 hierarchy and its standard V-cycle, back, smoothing
 template <typename T>
 __device__ void ho_run(const VCycle<T>& vc, int nu1, int nu2) {
+    HO_DECL();
     const HoDesc& H = *vc.ho;
     const int kd = vc.hkind, d = vc.P->dim, L = vc.P->L;
     const LevelDesc& F = vc.P->lev[L - 1];
@@ -408,10 +452,21 @@ __device__ void ho_run(const VCycle<T>& vc, int nu1, int nu2) {
     for (int i = threadIdx.x; i < F.n; i += blockDim.x) x[i] = 0;
     __syncthreads();
     for (int s = 0; s < nu1; ++s) {
-        vc.residual(L - 1);
+        {
+            HO_T0();
+            vc.residual(L - 1);
+            HO_T1(vc.phase, 52);
+        }
+        HO_T0();
         ho_smooth(vc);
+        HO_T1(vc.phase, 53);
     }
-    vc.residual(L - 1);
+    {
+        HO_T0();
+        vc.residual(L - 1);
+        HO_T1(vc.phase, 52);
+    }
+    HO_T0();
     // restriction P^T r into the right-hand side of the degree-1 hierarchy
     const VCycle<T>& cv = *vc.coarse;
     const int Lc = cv.P->L;
@@ -431,7 +486,13 @@ __device__ void ho_run(const VCycle<T>& vc, int nu1, int nu2) {
     for (int i = threadIdx.x; i < Cf.n; i += blockDim.x) bc[i] = 0;
     __syncthreads();
     free_add(bc, Cf.m, H.loc[kd], dims, cur);
-    cv.run(2, 2);
+    HO_T1(vc.phase, 54);
+    {
+        HO_T0();
+        cv.run(2, 2);
+        HO_T1(vc.phase, 55);
+    }
+    HO_T0();
     // prolongation P x_c
     free_gather(cv.X(Lc - 1), Cf.m, H.loc[kd], dims, vc.t1);
     cur = vc.t1;
@@ -444,9 +505,16 @@ __device__ void ho_run(const VCycle<T>& vc, int nu1, int nu2) {
         oth = t;
     }
     free_add(x, F.m, H.lof[kd], dims, cur);
+    HO_T1(vc.phase, 56);
     for (int s = 0; s < nu2; ++s) {
-        vc.residual(L - 1);
+        {
+            HO_T0();
+            vc.residual(L - 1);
+            HO_T1(vc.phase, 52);
+        }
+        HO_T0();
         ho_smooth(vc);
+        HO_T1(vc.phase, 53);
     }
 }
 
@@ -455,18 +523,25 @@ __device__ void ho_run(const VCycle<T>& vc, int nu1, int nu2) {
 // hierarchies' V-cycles at every site multiplies the compile time)
 template <typename T>
 __device__ __noinline__ void vcycle_apply(const VCycle<T>& vc, const double* rin, double* zout, int nu1, int nu2) {
+    HO_DECL();
     int L = vc.P->L;
     int n = vc.P->lev[L - 1].n;
     T* b = vc.B(L - 1);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) b[i] = (T)rin[i];
-    __syncthreads();
+    {
+        HO_T0();
+        for (int i = threadIdx.x; i < n; i += blockDim.x) b[i] = (T)rin[i];
+        __syncthreads();
+        HO_T1(vc.phase, 58);
+    }
     if (vc.ho)
         ho_run(vc, nu1, nu2);
     else
         vc.run(nu1, nu2);
     const T* x = vc.X(L - 1);
+    HO_T0();
     for (int i = threadIdx.x; i < n; i += blockDim.x) zout[i] = (double)x[i];
     __syncthreads();
+    HO_T1(vc.phase, 58);
 }
 
 // Euclidean projection on ker C for the rows of this patch (rows have
@@ -550,13 +625,19 @@ __global__ void __launch_bounds__(512) k_solve(SolveArgs a0) {
     VCycle<T> vc;
     vc.P = &P;
     vc.mask = kind == 0 ? P.dmask : allsides;
-    vc.alpha = (kind == 0 && P.floating) ? (T)a.alpha : T(0);
-    vc.K = a.mixed ? (const T*)(const void*)a.K32 : (const T*)(const void*)a.K64;
+    // floating patches (Neumann hierarchy): the values of K + alpha M^ built
+    // at set-up, so that the rows carry no mass terms
+    const bool floatN = kind == 0 && P.floating;
+    const T* KMv = a.mixed ? (const T*)(const void*)a.KM32 : (const T*)(const void*)a.KM64;
+    const bool reg = floatN && KMv != nullptr;
+    vc.alpha = (floatN && !reg) ? (T)a.alpha : T(0);
+    vc.K = reg ? KMv : (a.mixed ? (const T*)(const void*)a.K32 : (const T*)(const void*)a.K64);
     vc.tab = a.mixed ? (const T*)(const void*)a.tabf : (const T*)(const void*)a.tab;
     vc.itab = a.itab;
     vc.A0inv = (a.mixed ? (const T*)(const void*)a.A0inv32 : (const T*)(const void*)a.A0inv64) + P.a0off[kind];
     vc.lvec = (T*)a.lv + sd.lv;
     vc.nlvec = P.nlvec;
+    vc.phase = a.phase;
     // high-order multigrid: the degree-1 hierarchy of the companion problem
     // (same patch index) and the work tensors follow the slot's x | b | r
     VCycle<T> vco;
@@ -564,7 +645,7 @@ __global__ void __launch_bounds__(512) k_solve(SolveArgs a0) {
         const PatchDesc& Q = a.sub_pd[sd.patch];
         vco.P = &Q;
         vco.mask = vc.mask;
-        vco.alpha = vc.alpha;
+        vco.alpha = floatN ? (T)a.alpha : T(0);
         vco.K = a.mixed ? (const T*)(const void*)a.sub_K32 : (const T*)(const void*)a.sub_K64;
         vco.tab = a.mixed ? (const T*)(const void*)a.sub_tabf : (const T*)(const void*)a.sub_tab;
         vco.itab = a.sub_itab;
@@ -746,15 +827,18 @@ __global__ void __launch_bounds__(512) k_solve(SolveArgs a0) {
     }
 
     if (a.mode == MODE_VCYCLE || a.mode == MODE_VCYCLE_DIR) {
+        HO_DECL();
         const double* bb = a.in + P.toff;
         double* xx = a.out + P.toff;
         const int rmask = kind == 0 ? P.dmask : allsides;
         for (int c = 0; c < a.ncycles; ++c) {
+            HO_T0();
             for (int i = threadIdx.x; i < n; i += blockDim.x) {
                 int i0 = i % F.m[0], i1 = (i / F.m[0]) % F.m[1], i2 = i / (F.m[0] * F.m[1]);
                 r[i] = ieti_masked(rmask, F.m, i0, i1, i2) ? 0.0 : bb[i] - k64_row(P, a.K64, xx, i);
             }
             __syncthreads();
+            HO_T1(a.phase, 57);
             vcycle_apply(vc, r, z, a.nu1, a.nu2);
             for (int i = threadIdx.x; i < n; i += blockDim.x) xx[i] += z[i];
             __syncthreads();

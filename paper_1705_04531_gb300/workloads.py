@@ -183,6 +183,8 @@ def by_name(name: str, scale: Optional[int] = None) -> Domain:
         return annulus_6x6(max(4, 64 // s), 3)
     if name == "cube2x2x2_p2_n32":
         return cube_2x2x2(max(4, 32 // s), 2)
+    if name in ("annulus6x6_p4_n32", "annulus6x6_p7_n32"):
+        return annulus_6x6(max(4, 32 // s), int(name[len("annulus6x6_p")]))
     if name == "uneven8x8_s0":
         if s == 1:
             return uneven_8x8(0)
