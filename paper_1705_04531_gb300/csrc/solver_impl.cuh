@@ -106,7 +106,6 @@ struct GrpT {
             __syncthreads();
     }
 };
-using Grp = GrpT<true>;
 
 template <bool CL>
 __device__ __forceinline__ GrpT<CL> make_grp() {
