@@ -168,3 +168,21 @@ def test_ietidp_with_highorder_mg_equals_global_solve(case):
     its = [i for i in s.stats.neumann_its if i > 0]
     print(case, "outer", s.stats.outer_it, "mean Neumann CG iterations", np.mean(its))
     assert np.mean(its) < 40, np.mean(its)
+
+
+def test_highorder_mode_basis_equals_direct_basis():
+    """With the high-order multigrid the primal basis is still the solution of
+    Eq. 6 (computed with the standard V-cycle as the preconditioner): equal
+    to the direct basis, C Phi = I and Phi K-orthogonal to ker C, on curved
+    patches with a floating one at p = 4."""
+    dom = W.annulus_6x6(8, 4, grid=(3, 3))
+    a = O.IETIDP(dom, O.Options(mode="direct"))
+    b = O.IETIDP(dom, O.Options(mode="mg", mg_kind="highorder"))
+    rng = np.random.default_rng(3)
+    for k in range(a.N):
+        assert np.abs(a.phi[k] - b.phi[k]).max() < 1e-9
+        C, phi, K = b.C[k].toarray(), b.phi[k], b.K[k]
+        assert np.abs(C @ phi - np.eye(C.shape[0])).max() < 1e-12
+        v = rng.standard_normal(K.shape[0])
+        v -= C.T @ np.linalg.solve(C @ C.T, C @ v)
+        assert np.abs(phi.T @ (K @ v)).max() < 1e-9 * np.linalg.norm(K @ v)
