@@ -154,8 +154,11 @@ typedef struct ietidp_handle ietidp_handle;
  * and the first degree-1 level, and on the finest level a subspace-corrected
  * mass smoother (after Hofreither and Takacs, SIAM J. Numer. Anal. 55, 2017)
  * with a rank-one approximation of the geometry, applied by fast
- * diagonalization; Gauss-Seidel on the degree-1 levels.  HIGHORDER needs an
- * even element count per direction; 3D patches must be boxes. */
+ * diagonalization; Gauss-Seidel on the degree-1 levels.  The degree-1
+ * space has floor(n/2) elements per direction (at least 1); 3D patches must
+ * be boxes.  The primal basis (Eq. 6) is computed with the standard
+ * hierarchy in both settings (the smoother above may overshoot, which the
+ * Schoeberl-Zulehner CG does not allow); degrees up to 7. */
 #define IETIDP_MG_STANDARD  0
 #define IETIDP_MG_HIGHORDER 1
 
